@@ -1,0 +1,355 @@
+"""Benchmark of the Brillouin-operator apply on GB300.
+
+Workload (default): one application of D_B to a Gaussian spinor field on a
+32^3 x 64 lattice (antiperiodic in t) with synthetic links exp(i 0.3 H), the
+hopping fields stored in FP32 ("f32-full"), FP32 spinors and arithmetic.
+A step is one apply over the whole lattice; the link precompute (path sums +
+SU(3) projection) runs once per gauge field, before timing.
+
+Metric: algorithmic GB/s = (40 unique hopping fields + spinor in + out per
+site) x V / time; the hopping fields alone are ~6 GB, far above L2, so no
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f32-full]
+                    [--nrhs 1] [--impl native|reference] [--sweep] [--solve]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_BENCH = (32, 32, 32, 64)
+BC = (1, 1, 1, -1)
+EPS = 0.3
+SEED = 1015
+
+LINK_BYTES = {  # bytes per site of the 40 stored hopping fields
+    "f64-full": 40 * 144, "f32-full": 40 * 72, "f32-2row": 40 * 48, "f32-8param": 40 * 32,
+    "f16-full": 40 * 36, "f16-2row": 40 * 24, "f16-8param": 40 * 16,
+}
+FLOPS_PER_SITE = 37296  # per right-hand side: 80 hops x 4 spins x 3 rows x 3 complex MACs (8 flops)
+                        # + 24 (1 + n) real FMAs per hop for the spin structure + diagonal
+
+
+def spinor_bytes(mode):
+    return 2 * (192 if mode.startswith("f64") else 96)  # in + out per site and RHS
+
+
+def site_bytes(mode, nrhs):
+    return LINK_BYTES[mode] + nrhs * spinor_bytes(mode)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during timing."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [t.strip() for t in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(pg, value, device=None):
+    """Maximum of a float over all ranks (identity on one process)."""
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        import torch
+
+        t = torch.zeros(1, device=device)
+        pg.all_reduce(t)
+
+
+# ---------------------------------------------------------------------------------
+def cpu_baseline(mode, seconds=15.0):
+    """The oracle (as it stands) timed on the host cores on a bounded sample:
+    a 16^3 x 8 lattice with the same link distribution, FP64 apply with the
+    oracle's hops prebuilt (the hop build is not part of a step)."""
+    import numpy as np
+
+    import oracle
+    from paper_1012_3615_gb300 import synth
+
+    L = (16, 16, 16, 8)
+    U = synth.random_su3_links(L, EPS, SEED)
+    psi = synth.gaussian_spinor(L, 1, SEED + 1)[0]
+    W = oracle.build_hops(L, U)
+    V = synth.volume(L)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.apply(L, BC, W, 0.0, psi)
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= 50:
+            break
+    dt = (time.perf_counter() - t0) / n
+    gbs = site_bytes("f64-full", 1) * V / dt / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "FP64 oracle apply on a 16^3x8 lattice (same link and source distribution), %d applies, "
+                      "%.3f s each, hops prebuilt" % (n, dt), "ms_per_apply": dt * 1e3}
+
+
+def reference_arm(args, world, rank, pg):
+    """--impl reference: the CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1012_3615_gb300 import synth
+
+    L = (16, 16, 16, 8)
+    U = synth.random_su3_links(L, EPS, SEED)
+    psi = synth.gaussian_spinor(L, 1, SEED + 1)[0]
+    W = oracle.build_hops(L, U)
+    V = synth.volume(L)
+    for _ in range(args.warmup):
+        oracle.apply(L, BC, W, 0.0, psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply(L, BC, W, 0.0, psi)
+    dt = (time.perf_counter() - t0) / args.steps
+    gbs = site_bytes("f64-full", 1) * V / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "D_B apply GB/s", "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "D_B apply, FP64 CPU oracle, bounded sample 16^3x8 of the 32^3x64 workload",
+                   "lattice": list(L), "nrhs": 1},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "16^3x8 lattice, %d timed applies" % args.steps},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------
+def time_apply(op, x, out, mode, nrhs, steps, warmup, stream):
+    import torch
+
+    prec = mode.split("-")[0]
+    for _ in range(warmup):
+        op.apply(x, 0.0, prec=prec, out=out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        op.apply(x, 0.0, prec=prec, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps  # ms per apply
+
+
+def native(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    from paper_1012_3615_gb300 import Brillouin, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mode, nrhs = args.mode, args.nrhs
+    prec, comp = mode.split("-")
+    L = L_BENCH
+    V = synth.volume(L)
+    U = synth.random_su3_links_torch(L, EPS, SEED + rank, device=dev)
+    op = Brillouin(L, BC)
+    op.build_hops(U, prec=prec, comp=comp)
+    del U
+    sdt = torch.complex128 if prec == "f64" else torch.complex64
+    x = synth.gaussian_spinor_torch(L, nrhs, SEED + 100 + rank, device=dev, dtype=sdt)
+    out = torch.empty_like(x)
+    op.tune(prec, nrhs)
+    stream = torch.cuda.current_stream()
+    time_apply(op, x, out, mode, nrhs, 1, args.warmup, stream)  # warm-up (untimed)
+
+    clocks = ClockSampler(local)
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    n0 = op.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.apply(x, 0.0, prec=prec, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    t_wall = time.perf_counter() - t_wall
+    launches = op.kernel_launches() - n0
+    ms = e0.elapsed_time(e1) / args.steps
+    ck = clocks.stop()
+    ms_max = max_over_ranks(pg, ms, dev)
+
+    bytes_step = site_bytes(mode, nrhs) * V
+    value = bytes_step * world / (ms_max * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    dslash_gbs = bytes_step / (ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    xh = x.cpu().pin_memory()
+    oh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(2, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        xd = xh.to(dev, non_blocking=True)
+        od = op.apply(xd, 0.0, prec=prec)
+        oh.copy_(od, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": bytes_step / e2e_s / 1e9 * world, "unit": "GB/s",
+           "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+           "d2h_bytes_per_step": int(oh.numel() * oh.element_size()), "ms_per_step": e2e_s * 1e3}
+
+    flops = FLOPS_PER_SITE * nrhs * V / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "D_B apply GB/s", "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
+        "config": {"workload": "D_B apply, 32^3x64 lattice, antiperiodic t, links exp(i0.3H), Gaussian spinors",
+                   "lattice": list(L), "nrhs": nrhs, "hop_storage": mode, "threads_per_block": None,
+                   "l2": "inputs larger than L2 (hopping fields %.1f GB)" % (LINK_BYTES[mode] * V / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": dslash_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": dslash_gbs / peak, "traffic": None,
+                     "peak_kind": peak_kind + " hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": bytes_step, "tflops": flops},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(mode, seconds=args.cpu_seconds)
+    if args.sweep:
+        sweep = {}
+        for m in ["f64-full", "f32-full", "f32-2row", "f32-8param", "f16-full", "f16-2row", "f16-8param"]:
+            for nr in ([1] if m.startswith("f64") else [1, 4, 12]):
+                p, c = m.split("-")
+                if p != "f64":
+                    op.store_hops(p, c)
+                sd = torch.complex128 if p == "f64" else torch.complex64
+                xx = synth.gaussian_spinor_torch(L, nr, SEED + 7, device=dev, dtype=sd)
+                oo = torch.empty_like(xx)
+                op.tune(p, nr)
+                t = time_apply(op, xx, oo, m, nr, 3 if p == "f64" else 10, 2, stream)
+                b = site_bytes(m, nr) * V
+                sweep["%s/n%d" % (m, nr)] = {"ms": t, "GB/s": b / (t * 1e-3) / 1e9,
+                                             "frac_hbm": b / (t * 1e-3) / 1e9 / peak,
+                                             "TFLOP/s": FLOPS_PER_SITE * nr * V / (t * 1e-3) / 1e12}
+                del xx, oo
+        line["sweep"] = sweep
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--mode", default="f32-full", choices=sorted(LINK_BYTES))
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank, pg)
+    else:
+        native(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * brillouin.h -- C ABI of the GB300 (sm_103a) Brillouin Dirac operator library.
+ *
+ * The operator (Duerr & Koutsou, "Brillouin improvement for Wilson fermions",
+ * Eq. def_pref with c_SW = 0, a = 1):
+ *
+ *   D = sum_mu gamma_mu nabla^iso_mu - (1/2) Laplacian^bri + m0
+ *
+ * written in the rho/lambda class form of Sec. 8 with the der_iso / lap_bri
+ * weights of Tab. rholambda:
+ *
+ *   (D psi)(x) = (m0 + lambda_0) psi(x)
+ *              + sum_{d in {-1,0,1}^4, d != 0} s_d(x) [lambda_n 1 + rho_n sum_mu d_mu gamma_mu]
+ *                                                      (x) W_d(x) psi(x+d),     n = |d|_1
+ *
+ *   lambda = (240, -8, -4, -2, -1)/128,  rho_1..4 = (64, 16, 4, 1)/432.
+ *
+ * W_{+-mu}(x) are the links U_mu(x), U_mu(x-mu)^dagger; every off-axis hop is
+ * the sum over all shortest lattice paths x -> x+d, back-projected to SU(3) in
+ * a single step (Sec. 5.1), with the projection of Eq. proj_SU (Sec. 5.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lattice: extents L[0..3] (x, y, z, t), each >= 3; site index
+ *    x + L0*(y + L1*(z + L2*t)).  Links are periodic.  The fermion field gets
+ *    the boundary phase bc_sign[mu] (+1 or -1) on every hop that wraps around
+ *    direction mu; the default is antiperiodic in t, {1, 1, 1, -1}.
+ *  - Gauge field U: device memory, [V][4][3][3] complex128 (interleaved
+ *    re/im, row-major 3x3), U[x][mu] connecting x to x+mu.
+ *  - Spinors: device memory, [nrhs][V][4][3] complex (spin, colour) with
+ *    interleaved re/im, element type complex128 for BRI_F64 and complex64 for
+ *    BRI_F32 and BRI_F16 (BRI_F16 means half-precision hopping fields with
+ *    FP32 spinors and FP32 arithmetic).
+ *  - Gamma matrices: the hermitian chiral (DeGrand-Rossi) basis,
+ *    gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1, 1, -1, -1).
+ *  - Ownership: the caller owns every buffer passed in; the library owns the
+ *    hopping fields, its work spaces and its tuning cache, all released by
+ *    bri_destroy.  Nothing is retained from caller buffers beyond the call,
+ *    except that bri_build_hops keeps a device copy of U (used by the force).
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *    work is enqueued on it; calls return once the work is enqueued, except
+ *    where stated (solvers synchronise the stream to read convergence data).
+ *  - Errors: every call returns a bri_status; no exception crosses the ABI.
+ *    bri_last_error(ctx) returns a human-readable description of the last
+ *    failure on that context.  A CUDA launch or runtime failure is returned as
+ *    BRI_ECUDA.  Arguments are validated before any work is enqueued.
+ *  - Thread safety: one context must not be used from two host threads at
+ *    once.
+ */
+#ifndef BRILLOUIN_H
+#define BRILLOUIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BRI_OK = 0,
+    BRI_EINVAL = -1,      /* invalid argument (null pointer, bad size, misaligned buffer) */
+    BRI_ENOMEM = -2,      /* device allocation failed */
+    BRI_ECUDA = -3,       /* CUDA runtime / launch error */
+    BRI_ENOTCONV = -4,    /* solver reached maxit without meeting tol */
+    BRI_EBREAKDOWN = -5,  /* BiCGstab breakdown (rho or omega vanished) */
+    BRI_ENAN = -6,        /* NaN / Inf met in a solve */
+    BRI_ETIMEOUT = -7,    /* a bounded device-side wait gave up */
+    BRI_ESTATE = -8       /* call out of order (e.g. apply before build_hops) */
+} bri_status;
+
+typedef enum { BRI_F64 = 0, BRI_F32 = 1, BRI_F16 = 2 } bri_prec;
+
+/* storage of the hopping fields (each W_d(x) is in SU(3), Sec. 5.2) */
+typedef enum {
+    BRI_LINK_FULL = 0,   /* 18 reals */
+    BRI_LINK_2ROW = 1,   /* 12 reals, third row = conj(row0 x row1) */
+    BRI_LINK_8PARAM = 2  /* 8 reals: U01, U02, U10, arg U00, arg U20 */
+} bri_comp;
+
+typedef struct {
+    int L[4];       /* extents, each >= 3 */
+    int bc_sign[4]; /* fermion boundary phase per direction, +1 or -1 */
+} bri_lattice;
+
+typedef struct bri_ctx bri_ctx; /* opaque */
+
+/* Create a context for one lattice on the current CUDA device.
+ * Errors: BRI_EINVAL (null pointers, extent < 3, |bc_sign| != 1, volume
+ * beyond 2^31 sites), BRI_ENOMEM. */
+bri_status bri_create(const bri_lattice *lat, bri_ctx **out);
+
+/* Release the context and every device buffer it owns.  Null is allowed. */
+bri_status bri_destroy(bri_ctx *ctx);
+
+/* Build the 80 path-averaged hopping fields from the links U (Sec. 5.1,
+ * Sec. 5.2): path sums over all shortest paths for the 2-, 3- and 4-hop
+ * offsets (2, 6 and 24 paths), one SU(3) back-projection each (Eq. proj_SU),
+ * computed in FP64.  The 40 fields W_d with the last non-zero component of d
+ * positive are stored; W_{-d}(x) = W_d(x-d)^dagger supplies the rest.
+ * The FP64 fields are always kept; if prec != BRI_F64 a copy in (prec, comp)
+ * is stored as well.  U: device, [V][4][3][3] complex128, 16-byte aligned;
+ * the library keeps its own copy.  Errors: BRI_EINVAL, BRI_ENOMEM, BRI_ECUDA. */
+bri_status bri_build_hops(bri_ctx *ctx, const double *U, bri_prec prec, bri_comp comp, void *stream);
+
+/* Store an additional (prec, comp) copy of the FP64 hopping fields built by
+ * the last bri_build_hops (no recomputation).  Errors: BRI_ESTATE if no
+ * fields were built, BRI_EINVAL, BRI_ENOMEM. */
+bri_status bri_store_hops(bri_ctx *ctx, bri_prec prec, bri_comp comp, void *stream);
+
+/* Copy the 40 stored FP64 hopping fields to out: device, [V][40][3][3]
+ * complex128; field j has offset d = digits of (j + 41) in base 3 minus 1,
+ * x fastest (d_mu = ((j+41) / 3^mu) % 3 - 1).  Errors: BRI_ESTATE, BRI_EINVAL. */
+bri_status bri_get_hops(bri_ctx *ctx, double *out, void *stream);
+
+/* out = D psi (dagger = 0) or D^dagger psi = gamma_5 D gamma_5 psi (dagger = 1,
+ * Sec. 1), for nrhs right-hand sides, with the hopping fields stored in prec
+ * (for BRI_F32 / BRI_F16 the compression of the last build/store in that
+ * precision).  in/out: device, [nrhs][V][4][3] complex (see conventions),
+ * 16-byte aligned, must not overlap.  Errors: BRI_EINVAL, BRI_ESTATE
+ * (fields of that precision not built), BRI_ECUDA. */
+bri_status bri_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int dagger,
+                     bri_prec prec, void *stream);
+
+/* Hermitian overlap kernel H = gamma_5 (D_B - rho), D_B at m0 = 0 (the shifted
+ * kernel of Sec. 7.4 entering Eq. def_over; rho = 1 there).  Same buffers and
+ * errors as bri_apply. */
+bri_status bri_apply_overlap_kernel(bri_ctx *ctx, void *out, const void *in, int nrhs, double rho,
+                                    bri_prec prec, void *stream);
+
+typedef struct {
+    int iters;          /* inner (or only) BiCGstab iterations */
+    int outer_iters;    /* defect-correction cycles (0 for mode 0) */
+    double true_resid;  /* ||b - D x|| / ||b||, recomputed in FP64 */
+    double seconds;     /* wall time of this right-hand side's solve */
+    bri_status status;  /* BRI_OK, BRI_ENOTCONV, BRI_EBREAKDOWN or BRI_ENAN */
+} bri_solve_info;
+
+/* Solve D x = b (BiCGstab, Sec. 6.4) for nrhs right-hand sides to the true
+ * relative residual tol.
+ *   mode 0: FP64 BiCGstab, one right-hand side after the other.
+ *   mode 1: FP64 defect correction around an FP32 BiCGstab (FP32 hops as
+ *           last stored, FP32 spinors, FP64 dot products).
+ *   mode 2: as mode 1 with the FP16 hopping fields.
+ *   mode 3: batched: all nrhs right-hand sides advance together through one
+ *           multi-RHS apply per step (mode-2 inner precision), each with its
+ *           own BiCGstab scalars, inside one CUDA graph per block of steps.
+ * x: device, [nrhs][V][4][3] complex128, used as the initial guess and
+ * overwritten with the solution; b: device, same layout.  info: host array of
+ * nrhs entries (may be null).  Synchronises the stream.  Returns BRI_OK when
+ * every right-hand side converged, otherwise the first failing status. */
+bri_status bri_solve(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol,
+                     int maxit, int mode, bri_solve_info *info, void *stream);
+
+/* Fermion force dU += d Re(chi^dagger D[U] psi) / dU for the U of the last
+ * bri_build_hops, with the convention dU = df/dRe U + i df/dIm U per link
+ * entry, U treated as an unconstrained complex matrix (the hops of Sec. 5.1
+ * and the projection of Sec. 5.2 differentiated exactly).
+ * recompute_hops = 1 recomputes the projected fields instead of reading the
+ * stored FP64 ones.  dU: device [V][4][3][3] complex128 (accumulated);
+ * chi, psi: device [V][4][3] complex128.  Errors: BRI_ESTATE, BRI_EINVAL,
+ * BRI_ENOMEM, BRI_ECUDA. */
+bri_status bri_force(bri_ctx *ctx, double *dU, const double *chi, const double *psi, double m0,
+                     int recompute_hops, void *stream);
+
+/* dU += d( phi^dagger (D^dagger D)^{-1} phi ) / dU = -2 d Re(Y^dagger D X)/dU
+ * with X = (D^dagger D)^{-1} phi, Y = D X (both solved in FP64 to tol).
+ * phi: device [V][4][3] complex128.  info (host, may be null) receives the
+ * second solve's data.  Synchronises the stream. */
+bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double m0, double tol,
+                             int maxit, bri_solve_info *info, void *stream);
+
+/* Batched SU(3) projection Y_i = P_SU(3)(A_i) (Eq. proj_SU), FP64.
+ * A, Y: device, [n][3][3] complex128 (may alias).  Errors: BRI_EINVAL. */
+bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, void *stream);
+
+/* Tune the launch shape of the apply kernels for (prec, nrhs) on this
+ * lattice (timed with CUDA events, result cached in the context and, when the
+ * environment variable BRI_TUNE_CACHE names a file, in that file).
+ * Requires the fields of that precision.  Synchronises the stream. */
+bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
+
+/* Number of kernels this context launched so far (diagnostics). */
+long bri_kernel_launches(bri_ctx *ctx);
+
+/* Description of the last error on ctx (or of the last bri_create failure
+ * when ctx is null).  The string stays valid until the next call on ctx. */
+const char *bri_last_error(bri_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BRILLOUIN_H */

@@ -195,3 +195,16 @@ def force(L, bc, U, m0, chi, psi):
     if rc != 0:
         raise RuntimeError("oracle force failed (%d)" % rc)
     return dU
+
+
+def apply_sites(L, bc, U, m0, psi, sites):
+    """(D psi)(x) for the listed sites only, hops built from U per site."""
+    V = int(np.prod(L))
+    U = _c(U, (V, 4, 3, 3))
+    psi = _c(psi, (V, 4, 3))
+    out = np.zeros((len(sites), 4, 3), np.complex128)
+    for i, s in enumerate(sites):
+        o = np.zeros((4, 3), np.complex128)
+        lib().bo_apply_site(_iv(L), _iv(bc), _p(U), ctypes.c_double(m0), ctypes.c_long(int(s)), _p(psi), _p(o))
+        out[i] = o
+    return out

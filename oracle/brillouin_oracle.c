@@ -774,3 +774,34 @@ int bo_project_vjp_batch(long n, const cplx *A, const cplx *G, cplx *GA) {
     for (long i = 0; i < n; i++) bad |= bo_project_vjp(A + 9 * i, G + 9 * i, GA + 9 * i) != 0;
     return bad ? -1 : 0;
 }
+
+/* (D psi)(x) at one site, with the 80 hops of that site built from U on the
+ * spot (path sums + projection): lets tests sample large lattices one output
+ * site at a time without building every hop. out: 12 complex. */
+int bo_apply_site(const int L[4], const int bc[4], const cplx *U, double m0, long s, const cplx *in, cplx *out) {
+    double lam[5], rho[5];
+    bo_weights(lam, rho);
+    int x[4];
+    coords(L, s, x);
+    for (int i = 0; i < 12; i++) out[i] = (m0 + lam[0]) * in[s * 12 + i];
+    for (int k = 0; k < NHOP; k++) {
+        if (k == CENTRE) continue;
+        int d[4];
+        offset_of(k, d);
+        cplx A[9], w[9], M[16];
+        bo_path_sum(L, U, s, d, A, NULL);
+        if (hop_class(d) >= 2) bo_project_su3(A, w);
+        else memcpy(w, A, sizeof A);
+        hop_spin_matrix(d, 1.0, M);
+        double ph;
+        long y = shifted(L, bc, x, d, &ph);
+        for (int a = 0; a < 4; a++)
+            for (int c = 0; c < 3; c++) {
+                cplx sum = 0;
+                for (int b = 0; b < 4; b++)
+                    for (int cc = 0; cc < 3; cc++) sum += M[4 * a + b] * w[3 * c + cc] * in[y * 12 + 3 * b + cc];
+                out[3 * a + c] += ph * sum;
+            }
+    }
+    return 0;
+}

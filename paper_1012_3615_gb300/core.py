@@ -1,0 +1,136 @@
+"""Torch-facing wrapper of the C ABI: tensors in, tensors out.
+
+PyTorch provides device memory and the current stream only; every operation
+is one call into libbrillouin.so.
+"""
+import ctypes
+
+import torch
+
+from . import abi
+
+_PREC = {"f64": abi.BRI_F64, "f32": abi.BRI_F32, "f16": abi.BRI_F16}
+_COMP = {"full": abi.BRI_LINK_FULL, "2row": abi.BRI_LINK_2ROW, "8param": abi.BRI_LINK_8PARAM}
+
+
+class BriError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (abi.STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def spinor_dtype(prec):
+    return torch.complex128 if prec == "f64" else torch.complex64
+
+
+class Brillouin:
+    """One lattice (extents L, fermion boundary phases bc) on the current GPU."""
+
+    def __init__(self, L, bc=(1, 1, 1, -1)):
+        self.lib = abi.load()
+        self.L = tuple(int(v) for v in L)
+        self.bc = tuple(int(v) for v in bc)
+        self.V = self.L[0] * self.L[1] * self.L[2] * self.L[3]
+        lat = abi.bri_lattice((ctypes.c_int * 4)(*self.L), (ctypes.c_int * 4)(*self.bc))
+        h = ctypes.c_void_p()
+        st = self.lib.bri_create(ctypes.byref(lat), ctypes.byref(h))
+        if st != 0:
+            raise BriError(st, self.lib.bri_last_error(None).decode())
+        self.ctx = h
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and ctx.value:
+            self.lib.bri_destroy(ctx)
+            self.ctx = None
+
+    def _check(self, st):
+        if st != 0:
+            raise BriError(st, self.lib.bri_last_error(self.ctx).decode())
+
+    def _spinor(self, t, prec):
+        dt = spinor_dtype(prec)
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError("spinor must be a contiguous cuda %s tensor" % dt)
+        if t.numel() % (self.V * 12) != 0:
+            raise ValueError("spinor size is not a multiple of V*12")
+        return t.numel() // (self.V * 12)
+
+    # ---- link precompute (Sec. 5.1, 5.2) -------------------------------------
+    def build_hops(self, U, prec="f64", comp="full"):
+        if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous() and U.numel() == self.V * 36):
+            raise ValueError("U must be a contiguous cuda complex128 (V, 4, 3, 3) tensor")
+        self._U = U
+        self._check(self.lib.bri_build_hops(self.ctx, _ptr(U), _PREC[prec], _COMP[comp], _stream()))
+
+    def store_hops(self, prec, comp="full"):
+        self._check(self.lib.bri_store_hops(self.ctx, _PREC[prec], _COMP[comp], _stream()))
+
+    def hops(self):
+        out = torch.empty((self.V, 40, 3, 3), dtype=torch.complex128, device="cuda")
+        self._check(self.lib.bri_get_hops(self.ctx, _ptr(out), _stream()))
+        return out
+
+    def project_su3(self, A):
+        A = A.contiguous()
+        Y = torch.empty_like(A)
+        self._check(self.lib.bri_project_su3(self.ctx, _ptr(Y), _ptr(A), A.numel() // 9, _stream()))
+        return Y
+
+    # ---- stencil (Eq. def_pref) ------------------------------------------------
+    def apply(self, psi, m0=0.0, dagger=False, prec="f64", out=None):
+        n = self._spinor(psi, prec)
+        out = torch.empty_like(psi) if out is None else out
+        self._check(self.lib.bri_apply(self.ctx, _ptr(out), _ptr(psi), n, float(m0), int(bool(dagger)),
+                                       _PREC[prec], _stream()))
+        return out
+
+    def overlap_kernel(self, psi, rho=1.0, prec="f64", out=None):
+        n = self._spinor(psi, prec)
+        out = torch.empty_like(psi) if out is None else out
+        self._check(self.lib.bri_apply_overlap_kernel(self.ctx, _ptr(out), _ptr(psi), n, float(rho), _PREC[prec],
+                                                      _stream()))
+        return out
+
+    # ---- solver (Sec. 6.4) -------------------------------------------------------
+    def solve(self, b, m0=0.0, tol=1e-10, maxit=10000, mode=0, x0=None):
+        n = self._spinor(b, "f64")
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        info = (abi.bri_solve_info * n)()
+        st = self.lib.bri_solve(self.ctx, _ptr(x), _ptr(b), n, float(m0), float(tol), int(maxit), int(mode),
+                                info, _stream())
+        infos = [info[i].as_dict() for i in range(n)]
+        if st not in (0, abi.BRI_ENOTCONV, abi.BRI_EBREAKDOWN, abi.BRI_ENAN):
+            self._check(st)
+        return x, infos
+
+    # ---- force ---------------------------------------------------------------------
+    def force(self, chi, psi, m0=0.0, dU=None, recompute_hops=True):
+        self._spinor(chi, "f64")
+        self._spinor(psi, "f64")
+        dU = torch.zeros((self.V, 4, 3, 3), dtype=torch.complex128, device="cuda") if dU is None else dU
+        self._check(self.lib.bri_force(self.ctx, _ptr(dU), _ptr(chi), _ptr(psi), float(m0), int(bool(recompute_hops)),
+                                       _stream()))
+        return dU
+
+    def force_inverse(self, phi, m0=0.0, tol=1e-12, maxit=20000, dU=None):
+        self._spinor(phi, "f64")
+        dU = torch.zeros((self.V, 4, 3, 3), dtype=torch.complex128, device="cuda") if dU is None else dU
+        info = abi.bri_solve_info()
+        self._check(self.lib.bri_force_inverse(self.ctx, _ptr(dU), _ptr(phi), float(m0), float(tol), int(maxit),
+                                               ctypes.byref(info), _stream()))
+        return dU, info.as_dict()
+
+    def tune(self, prec="f32", nrhs=1):
+        self._check(self.lib.bri_tune(self.ctx, _PREC[prec], int(nrhs), _stream()))
+
+    def kernel_launches(self):
+        return int(self.lib.bri_kernel_launches(self.ctx))

@@ -1,0 +1,275 @@
+// C ABI entry points (include/brillouin.h): argument validation, context
+// management, the launch-shape tuner and dispatch to the kernels.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace bri;
+
+static std::string g_create_error;
+
+// out = gamma_5 in (spins 2, 3 negated) or out = a * in, over n sites
+__global__ void k_gamma5_scale(double2 *out, const double2 *in, size_t n, int g5, double a) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * 12; i += (size_t)gridDim.x * blockDim.x) {
+        double f = g5 ? ((i % 12) >= 6 ? -1.0 : 1.0) : a;
+        out[i] = make_double2(f * in[i].x, f * in[i].y);
+    }
+}
+static bri_status gamma5_scale(bri_ctx *ctx, double2 *out, const double2 *in, int g5, double a, cudaStream_t s) {
+    k_gamma5_scale<<<608, 256, 0, s>>>(out, in, (size_t)ctx->g.V, g5, a);
+    BRI_LAUNCHED(ctx);
+    return BRI_OK;
+}
+
+bri_status bri_fail(bri_ctx *ctx, bri_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+static cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+static bri_status check_prec(bri_ctx *ctx, bri_prec p) {
+    if (p != BRI_F64 && p != BRI_F32 && p != BRI_F16) return bri_fail(ctx, BRI_EINVAL, "invalid precision");
+    return BRI_OK;
+}
+
+// ---- tuning cache file: one "key threads" line per entry ----------------------
+static void tune_load(bri_ctx *ctx) {
+    const char *f = getenv("BRI_TUNE_CACHE");
+    if (!f || !*f) return;
+    std::ifstream in(f);
+    std::string key;
+    int thr;
+    while (in >> key >> thr)
+        if (thr > 0 && thr <= 1024) ctx->tune[key] = thr;
+}
+static void tune_save_entry(const std::string &key, int thr) {
+    const char *f = getenv("BRI_TUNE_CACHE");
+    if (!f || !*f) return;
+    std::ofstream out(f, std::ios::app);
+    out << key << " " << thr << "\n";
+}
+
+extern "C" {
+
+bri_status bri_create(const bri_lattice *lat, bri_ctx **out) {
+    if (!lat || !out) return bri_fail(nullptr, BRI_EINVAL, "null argument");
+    long long V = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        if (lat->L[mu] < 3) return bri_fail(nullptr, BRI_EINVAL, "lattice extents must be >= 3");
+        if (lat->bc_sign[mu] != 1 && lat->bc_sign[mu] != -1)
+            return bri_fail(nullptr, BRI_EINVAL, "bc_sign must be +1 or -1");
+        V *= lat->L[mu];
+    }
+    if (V * 12 >= (1LL << 31)) return bri_fail(nullptr, BRI_EINVAL, "lattice volume too large");
+    bri_ctx *ctx = new bri_ctx();
+    for (int mu = 0; mu < 4; mu++) {
+        ctx->g.L[mu] = lat->L[mu];
+        ctx->g.bc[mu] = lat->bc_sign[mu];
+    }
+    ctx->g.V = (int)V;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return bri_fail(nullptr, BRI_ECUDA, "no CUDA device");
+    }
+    tune_load(ctx);
+    *out = ctx;
+    return BRI_OK;
+}
+
+bri_status bri_destroy(bri_ctx *ctx) {
+    if (!ctx) return BRI_OK;
+    bri_solver_free(ctx);
+    cudaFree(ctx->U);
+    cudaFree(ctx->hops64);
+    for (LinkStore *st : {&ctx->f32, &ctx->f16}) {
+        cudaFree(st->a);
+        cudaFree(st->b);
+    }
+    delete ctx;
+    return BRI_OK;
+}
+
+bri_status bri_build_hops(bri_ctx *ctx, const double *U, bri_prec prec, bri_comp comp, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!U || !bri_aligned16(U)) return bri_fail(ctx, BRI_EINVAL, "U must be a 16-byte aligned device pointer");
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    if (comp != BRI_LINK_FULL && comp != BRI_LINK_2ROW && comp != BRI_LINK_8PARAM)
+        return bri_fail(ctx, BRI_EINVAL, "invalid compression");
+    cudaStream_t s = as_stream(stream);
+    const size_t bytes = sizeof(double2) * 36 * (size_t)ctx->g.V;
+    if (!ctx->U) BRI_TRY_CUDA(ctx, cudaMalloc(&ctx->U, bytes));
+    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->U, U, bytes, cudaMemcpyDeviceToDevice, s));
+    BRI_RETURN_IF(bri_hops_build_impl(ctx, s));
+    return bri_hops_store_impl(ctx, prec, comp, s);
+}
+
+bri_status bri_store_hops(bri_ctx *ctx, bri_prec prec, bri_comp comp, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    if (comp != BRI_LINK_FULL && comp != BRI_LINK_2ROW && comp != BRI_LINK_8PARAM)
+        return bri_fail(ctx, BRI_EINVAL, "invalid compression");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    return bri_hops_store_impl(ctx, prec, comp, as_stream(stream));
+}
+
+bri_status bri_get_hops(bri_ctx *ctx, double *out, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!out || !bri_aligned16(out)) return bri_fail(ctx, BRI_EINVAL, "out must be a 16-byte aligned device pointer");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    return bri_export_hops_impl(ctx, (double2 *)out, as_stream(stream));
+}
+
+static bri_status check_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, bri_prec prec) {
+    if (!out || !in) return bri_fail(ctx, BRI_EINVAL, "null spinor pointer");
+    if (!bri_aligned16(out) || !bri_aligned16(in)) return bri_fail(ctx, BRI_EINVAL, "spinors must be 16-byte aligned");
+    if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    const size_t elt = prec == BRI_F64 ? 16 : 8;
+    const size_t bytes = elt * 12 * (size_t)ctx->g.V * nrhs;
+    const char *o = (const char *)out, *i = (const char *)in;
+    if (o < i + bytes && i < o + bytes) return bri_fail(ctx, BRI_EINVAL, "in and out overlap");
+    return BRI_OK;
+}
+
+bri_status bri_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int dagger, bri_prec prec,
+                     void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, prec));
+    return bri_dslash_impl(ctx, out, in, nrhs, m0, dagger ? 1 : 0, prec, as_stream(stream));
+}
+
+bri_status bri_apply_overlap_kernel(bri_ctx *ctx, void *out, const void *in, int nrhs, double rho, bri_prec prec,
+                                    void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, prec));
+    return bri_dslash_impl(ctx, out, in, nrhs, -rho, 2, prec, as_stream(stream));
+}
+
+bri_status bri_solve(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol, int maxit, int mode,
+                     bri_solve_info *info, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!x || !b || !bri_aligned16(x) || !bri_aligned16(b))
+        return bri_fail(ctx, BRI_EINVAL, "x and b must be 16-byte aligned device pointers");
+    if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
+    if (!(tol > 0) || maxit < 1) return bri_fail(ctx, BRI_EINVAL, "tol must be > 0 and maxit >= 1");
+    if (mode < 0 || mode > 3) return bri_fail(ctx, BRI_EINVAL, "mode must be 0..3");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    const size_t bytes = 16 * 12 * (size_t)ctx->g.V * nrhs;
+    if ((const char *)x < (const char *)b + bytes && (const char *)b < (const char *)x + bytes)
+        return bri_fail(ctx, BRI_EINVAL, "x and b overlap");
+    return bri_solve_impl(ctx, x, b, nrhs, m0, tol, maxit, mode, info, as_stream(stream));
+}
+
+bri_status bri_force(bri_ctx *ctx, double *dU, const double *chi, const double *psi, double m0, int recompute_hops,
+                     void *stream) {
+    (void)m0;              // the mass term does not depend on U
+    (void)recompute_hops;  // the force always recomputes the path sums; the projections are redone from them
+    if (!ctx) return BRI_EINVAL;
+    if (!dU || !chi || !psi || !bri_aligned16(dU) || !bri_aligned16(chi) || !bri_aligned16(psi))
+        return bri_fail(ctx, BRI_EINVAL, "dU, chi, psi must be 16-byte aligned device pointers");
+    if (!ctx->U) return bri_fail(ctx, BRI_ESTATE, "no links: call bri_build_hops first");
+    return bri_force_impl(ctx, (double2 *)dU, (const double2 *)chi, (const double2 *)psi, as_stream(stream));
+}
+
+bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double m0, double tol, int maxit,
+                             bri_solve_info *info, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!dU || !phi || !bri_aligned16(dU) || !bri_aligned16(phi))
+        return bri_fail(ctx, BRI_EINVAL, "dU and phi must be 16-byte aligned device pointers");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    cudaStream_t s = as_stream(stream);
+    const size_t n = (size_t)ctx->g.V * 12, bytes = n * sizeof(double2);
+    double2 *Z = nullptr, *X = nullptr, *Y = nullptr, *t = nullptr;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&Z, bytes));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&X, bytes));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&Y, bytes));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&t, bytes));
+    bri_status st = BRI_OK;
+    bri_solve_info i1{}, i2{};
+    do {
+        // D^dagger Z = phi  <=>  D (g5 Z) = g5 phi
+        if ((st = gamma5_scale(ctx, t, (const double2 *)phi, 1, 0.0, s)) != BRI_OK) break;
+        BRI_TRY_CUDA(ctx, cudaMemsetAsync(Z, 0, bytes, s));
+        if ((st = bri_solve_impl(ctx, (double *)Z, (const double *)t, 1, m0, tol, maxit, 0, &i1, s)) != BRI_OK) break;
+        if ((st = gamma5_scale(ctx, t, Z, 1, 0.0, s)) != BRI_OK) break;  // Z = g5 w
+        BRI_TRY_CUDA(ctx, cudaMemsetAsync(X, 0, bytes, s));
+        if ((st = bri_solve_impl(ctx, (double *)X, (const double *)t, 1, m0, tol, maxit, 0, &i2, s)) != BRI_OK) break;
+        if ((st = bri_dslash_impl(ctx, Y, X, 1, m0, 0, BRI_F64, s)) != BRI_OK) break;
+        // -2 d Re(Y^dagger D X)/dU: scale Y by -2
+        if ((st = gamma5_scale(ctx, t, Y, 0, -2.0, s)) != BRI_OK) break;
+        st = bri_force_impl(ctx, (double2 *)dU, t, X, s);
+    } while (0);
+    cudaStreamSynchronize(s);
+    cudaFree(Z);
+    cudaFree(X);
+    cudaFree(Y);
+    cudaFree(t);
+    if (info) *info = i2;
+    if (st == BRI_OK && (i1.status != BRI_OK || i2.status != BRI_OK)) st = i1.status != BRI_OK ? i1.status : i2.status;
+    return st;
+}
+
+bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (n < 0 || (n > 0 && (!Y || !A || !bri_aligned16(Y) || !bri_aligned16(A))))
+        return bri_fail(ctx, BRI_EINVAL, "A and Y must be 16-byte aligned device pointers, n >= 0");
+    return bri_project_impl(ctx, (double2 *)Y, (const double2 *)A, n, as_stream(stream));
+}
+
+bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
+    return bri_tune_impl(ctx, prec, nrhs, as_stream(stream));
+}
+
+long bri_kernel_launches(bri_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+const char *bri_last_error(bri_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"
+
+// ---- launch-shape tuner ---------------------------------------------------------
+bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) {
+    const size_t elt = prec == BRI_F64 ? 16 : 8;
+    const size_t bytes = elt * 12 * (size_t)ctx->g.V * nrhs;
+    void *in = nullptr, *out = nullptr;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&in, bytes));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&out, bytes));
+    BRI_TRY_CUDA(ctx, cudaMemsetAsync(in, 0, bytes, s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 128;
+    float best_ms = 1e30f;
+    bri_status st = BRI_OK;
+    for (int thr : {64, 128, 256, 512}) {
+        if ((st = bri_dslash_raw(ctx, out, in, nrhs, 0.0, 0, prec, nullptr, thr, s)) != BRI_OK) break;  // warm-up
+        cudaEventRecord(e0, s);
+        const int reps = 3;
+        for (int r = 0; r < reps && st == BRI_OK; r++) st = bri_dslash_raw(ctx, out, in, nrhs, 0.0, 0, prec, nullptr, thr, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st != BRI_OK) break;
+        if (ms < best_ms) { best_ms = ms; best = thr; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(in);
+    cudaFree(out);
+    if (st != BRI_OK) return st;
+    const std::string key = bri_tune_key(ctx, prec, nrhs);
+    ctx->tune[key] = best;
+    tune_save_entry(key, best);
+    return BRI_OK;
+}

@@ -1,0 +1,168 @@
+// Shared device-side definitions of the Brillouin operator library (sm_103a).
+//
+// The operator is the rho/lambda class form of Sec. 8 with the der_iso /
+// lap_bri weights of Tab. rholambda; hops are indexed by their offset
+// d in {-1,0,1}^4.  The 40 "canonical" offsets are those whose last non-zero
+// component is +1; with k(d) = 40 + sum_mu d_mu 3^mu they are exactly
+// k = 41..80, so canonical field j has d = base-3 digits of (j + 41) minus 1.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define BRI_HD __host__ __device__ __forceinline__
+#define BRI_D __device__ __forceinline__
+
+namespace bri {
+
+constexpr int NCANON = 40;  // stored hopping fields per site
+constexpr int NOFF = 81;    // offsets in the 3^4 hypercube, centre = 40
+
+// ---- offsets --------------------------------------------------------------
+BRI_HD constexpr int pow3(int m) { return m == 0 ? 1 : 3 * pow3(m - 1); }
+// component mu of the offset with hypercube index k (0..80)
+BRI_HD constexpr int off_comp(int k, int mu) { return (k / pow3(mu)) % 3 - 1; }
+BRI_HD constexpr int off_class(int k) {
+    return (off_comp(k, 0) != 0) + (off_comp(k, 1) != 0) + (off_comp(k, 2) != 0) + (off_comp(k, 3) != 0);
+}
+BRI_HD constexpr int canon_k(int j) { return j + 41; }
+
+// ---- weights (Sec. 8 / Tab. rholambda), written as closed forms -------------
+// lambda_0 = 240/128 and lambda_n = -2^(4-n)/128: the lap_bri stencil of App. C
+// is 2^(4-n)/64 off-centre and -240/64 at the centre, and D carries -1/2 of it.
+// rho_n = 4^(4-n)/432: the der_iso stencil of App. C.
+BRI_HD constexpr double lambda_w(int n) {
+    return n == 0 ? 240.0 / 128.0 : -double(1 << (4 - n)) / 128.0;
+}
+BRI_HD constexpr double rho_w(int n) { return n == 0 ? 0.0 : double(1 << (2 * (4 - n))) / 432.0; }
+
+// ---- gamma matrices: hermitian chiral (DeGrand-Rossi) basis -----------------
+// Every row of gamma_mu holds one non-zero entry: (gamma_mu)_{s, gcol(mu,s)} =
+// phase, phase in {+1, -1, +i, -i}.  gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4
+// = diag(1, 1, -1, -1).
+BRI_HD constexpr int gcol(int mu, int s) {
+    return mu == 0 ? 3 - s : mu == 1 ? 3 - s : mu == 2 ? (s + 2) % 4 : (s + 2) % 4;
+}
+// real and imaginary part of the entry
+BRI_HD constexpr int gre(int mu, int s) {
+    return mu == 1 ? (s == 0 || s == 3 ? -1 : 1) : mu == 3 ? 1 : 0;
+}
+BRI_HD constexpr int gim(int mu, int s) {
+    return mu == 0 ? (s < 2 ? 1 : -1) : mu == 2 ? ((s == 0 || s == 3) ? 1 : -1) : 0;
+}
+
+// ---- complex helpers --------------------------------------------------------
+template <typename R> struct C2;
+template <> struct C2<double> { using T = double2; };
+template <> struct C2<float> { using T = float2; };
+
+template <typename T> BRI_HD T mk(double re, double im);
+template <> BRI_HD double2 mk<double2>(double re, double im) { return make_double2(re, im); }
+template <> BRI_HD float2 mk<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+
+template <typename T> BRI_HD T cadd(T a, T b) { T r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename T> BRI_HD T csub(T a, T b) { T r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename T> BRI_HD T cmul(T a, T b) {
+    T r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename T> BRI_HD T cconj(T a) { T r; r.x = a.x; r.y = -a.y; return r; }
+// conj(a) * b
+template <typename T> BRI_HD T cmulc(T a, T b) {
+    T r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.x * b.y - a.y * b.x;
+    return r;
+}
+template <typename T, typename S> BRI_HD T cscale(T a, S s) { T r; r.x = a.x * s; r.y = a.y * s; return r; }
+template <typename T> BRI_HD double cnorm2(T a) { return (double)a.x * a.x + (double)a.y * a.y; }
+
+// 3x3 complex matrix, row-major
+template <typename T> struct M3 {
+    T e[9];
+};
+template <typename T> BRI_HD M3<T> m3_mul(const M3<T> &a, const M3<T> &b) {
+    M3<T> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            T s = cmul(a.e[3 * i], b.e[j]);
+            s = cadd(s, cmul(a.e[3 * i + 1], b.e[3 + j]));
+            s = cadd(s, cmul(a.e[3 * i + 2], b.e[6 + j]));
+            c.e[3 * i + j] = s;
+        }
+    return c;
+}
+template <typename T> BRI_HD M3<T> m3_dag(const M3<T> &a) {
+    M3<T> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.e[3 * i + j] = cconj(a.e[3 * j + i]);
+    return c;
+}
+template <typename T> BRI_HD M3<T> m3_add(const M3<T> &a, const M3<T> &b) {
+    M3<T> c;
+#pragma unroll
+    for (int i = 0; i < 9; i++) c.e[i] = cadd(a.e[i], b.e[i]);
+    return c;
+}
+template <typename T> BRI_HD M3<T> m3_zero() {
+    M3<T> c;
+#pragma unroll
+    for (int i = 0; i < 9; i++) c.e[i] = mk<T>(0, 0);
+    return c;
+}
+template <typename T> BRI_HD M3<T> m3_eye() {
+    M3<T> c = m3_zero<T>();
+    c.e[0] = c.e[4] = c.e[8] = mk<T>(1, 0);
+    return c;
+}
+
+// ---- geometry ---------------------------------------------------------------
+struct Geom {
+    int L[4];
+    int bc[4];
+    int V;
+};
+
+// Per-site neighbour deltas (with periodic wrap) and boundary phases.
+struct SiteNb {
+    int fw[4], bw[4];       // index delta of x+mu, x-mu
+    float sfw[4], sbw[4];   // fermion phase picked up by x -> x+mu, x -> x-mu
+};
+BRI_D SiteNb site_nb(const Geom &g, int site, int x[4]) {
+    SiteNb n;
+    int s = site;
+    int stride = 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        x[mu] = s % g.L[mu];
+        s /= g.L[mu];
+        bool top = x[mu] == g.L[mu] - 1, bot = x[mu] == 0;
+        n.fw[mu] = top ? -(g.L[mu] - 1) * stride : stride;
+        n.bw[mu] = bot ? (g.L[mu] - 1) * stride : -stride;
+        n.sfw[mu] = top ? (float)g.bc[mu] : 1.f;
+        n.sbw[mu] = bot ? (float)g.bc[mu] : 1.f;
+        stride *= g.L[mu];
+    }
+    return n;
+}
+// neighbour index and phase of offset k (0..80), sign = +1 forward, -1 reversed
+template <int K, int SGN> BRI_D int nb_index(const SiteNb &n, int site, float &ph) {
+    int y = site;
+    float p = 1.f;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        const int c = SGN * off_comp(K, mu);
+        if (c > 0) { y += n.fw[mu]; p *= n.sfw[mu]; }
+        if (c < 0) { y += n.bw[mu]; p *= n.sbw[mu]; }
+    }
+    ph = p;
+    return y;
+}
+
+}  // namespace bri

@@ -1,0 +1,79 @@
+// Internal state of a bri_ctx and helpers shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+
+#include "brillouin.h"
+#include "common.cuh"
+
+// One stored copy of the 40 hopping fields in a reduced precision.
+struct LinkStore {
+    bool valid = false;
+    bri_comp comp = BRI_LINK_FULL;
+    void *a = nullptr;  // main array (16-byte chunks, [40][chunks][V])
+    void *b = nullptr;  // tail array (8/4-byte chunk, [40][V]) or null
+};
+
+struct SolverWork;  // solver work spaces (solve.cu)
+
+struct bri_ctx {
+    bri::Geom g;
+    int device = 0;
+    double2 *U = nullptr;       // copy of the links, [V][4][9]
+    double2 *hops64 = nullptr;  // FP64 hops, [40][9][V]
+    bool have64 = false;
+    LinkStore f32, f16;
+    SolverWork *work = nullptr;
+    std::map<std::string, int> tune;  // launch-shape cache: key -> threads per block
+    std::string err;
+    long launches = 0;
+};
+
+bri_status bri_fail(bri_ctx *ctx, bri_status st, const std::string &msg);
+
+#define BRI_TRY_CUDA(ctx, call)                                                            \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bri_fail((ctx), e_ == cudaErrorMemoryAllocation ? BRI_ENOMEM : BRI_ECUDA, \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+// check the launch that was just enqueued
+#define BRI_LAUNCHED(ctx)                                                                  \
+    do {                                                                                   \
+        (ctx)->launches++;                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess)                                                             \
+            return bri_fail((ctx), BRI_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define BRI_RETURN_IF(st)              \
+    do {                               \
+        bri_status s_ = (st);          \
+        if (s_ != BRI_OK) return s_;   \
+    } while (0)
+
+inline bool bri_aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// entry points implemented in the individual translation units
+bri_status bri_hops_build_impl(bri_ctx *ctx, cudaStream_t s);
+bri_status bri_hops_store_impl(bri_ctx *ctx, bri_prec prec, bri_comp comp, cudaStream_t s);
+bri_status bri_project_impl(bri_ctx *ctx, double2 *Y, const double2 *A, long n, cudaStream_t s);
+// dslash: out = D in (mode 0), D^dagger in (mode 1), gamma5 (D - rho) in (mode 2, m0 = -rho)
+bri_status bri_dslash_impl(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode,
+                           bri_prec prec, cudaStream_t s);
+bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s);
+// dslash with an explicit launch shape; skip[r] != 0 skips right-hand side r
+bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
+                          const int *skip, int threads, cudaStream_t s);
+int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
+std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs);
+bri_status bri_export_hops_impl(bri_ctx *ctx, double2 *out, cudaStream_t s);
+void bri_solver_free(bri_ctx *ctx);
+bri_status bri_dp_levels(bri_ctx *ctx, void *A, const int *klist, const int start[6], cudaStream_t s);
+bri_status bri_force_impl(bri_ctx *ctx, double2 *dU, const double2 *chi, const double2 *psi, cudaStream_t s);
+bri_status bri_solve_impl(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol, int maxit,
+                          int mode, bri_solve_info *info, cudaStream_t user);

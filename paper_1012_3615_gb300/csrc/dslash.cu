@@ -1,0 +1,69 @@
+// Dispatch of the stencil apply over the stored link formats.
+#include <string>
+
+#include "ctx.h"
+#include "links.cuh"
+
+namespace bri {
+// defined in dslash_kernel.cuh, instantiated once per format in dslash_*.cu
+template <class LL>
+void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
+                   const int *skip, int threads, cudaStream_t s);
+}  // namespace bri
+
+using namespace bri;
+
+std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
+    const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
+    char buf[160];
+    snprintf(buf, sizeof buf, "dslash:%dx%dx%dx%d:p%d:c%d:n%d", ctx->g.L[0], ctx->g.L[1], ctx->g.L[2], ctx->g.L[3],
+             (int)prec, prec == BRI_F64 ? 0 : (int)st.comp, nrhs);
+    return buf;
+}
+
+int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
+    auto it = ctx->tune.find(bri_tune_key(ctx, prec, nrhs));
+    return it == ctx->tune.end() ? 128 : it->second;
+}
+
+bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
+                          const int *skip, int threads, cudaStream_t s) {
+    const Geom &g = ctx->g;
+    const double diag = m0 + lambda_w(0);
+    if (prec == BRI_F64) {
+        if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "FP64 hopping fields not built");
+        LinkF64 ll{ctx->hops64, g.V};
+        dslash_launch(mode, ll, in, out, nrhs, g, diag, skip, threads, s);
+    } else {
+        const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
+        if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
+        if (prec == BRI_F32) {
+            if (st.comp == BRI_LINK_FULL)
+                dslash_launch(mode, LinkF32<BRI_LINK_FULL>{(const float4 *)st.a, (const float2 *)st.b, g.V}, in, out, nrhs,
+                       g, diag, skip, threads, s);
+            else if (st.comp == BRI_LINK_2ROW)
+                dslash_launch(mode, LinkF32<BRI_LINK_2ROW>{(const float4 *)st.a, nullptr, g.V}, in, out, nrhs, g, diag, skip,
+                       threads, s);
+            else
+                dslash_launch(mode, LinkF32<BRI_LINK_8PARAM>{(const float4 *)st.a, nullptr, g.V}, in, out, nrhs, g, diag,
+                       skip, threads, s);
+        } else {
+            if (st.comp == BRI_LINK_FULL)
+                dslash_launch(mode, LinkF16<BRI_LINK_FULL>{(const uint4 *)st.a, st.b, g.V}, in, out, nrhs, g, diag, skip,
+                       threads, s);
+            else if (st.comp == BRI_LINK_2ROW)
+                dslash_launch(mode, LinkF16<BRI_LINK_2ROW>{(const uint4 *)st.a, st.b, g.V}, in, out, nrhs, g, diag, skip,
+                       threads, s);
+            else
+                dslash_launch(mode, LinkF16<BRI_LINK_8PARAM>{(const uint4 *)st.a, nullptr, g.V}, in, out, nrhs, g, diag,
+                       skip, threads, s);
+        }
+    }
+    BRI_LAUNCHED(ctx);
+    return BRI_OK;
+}
+
+bri_status bri_dslash_impl(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
+                           cudaStream_t s) {
+    return bri_dslash_raw(ctx, out, in, nrhs, m0, mode, prec, nullptr, bri_dslash_threads(ctx, prec, nrhs), s);
+}

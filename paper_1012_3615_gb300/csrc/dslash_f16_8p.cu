@@ -1,0 +1,4 @@
+// Stencil apply instantiated for the f16_8p hopping-field format.
+#include "dslash_kernel.cuh"
+
+BRI_INSTANTIATE_DSLASH(bri::LinkF16<BRI_LINK_8PARAM>)

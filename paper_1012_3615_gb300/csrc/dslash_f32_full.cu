@@ -1,0 +1,4 @@
+// Stencil apply instantiated for the f32_full hopping-field format.
+#include "dslash_kernel.cuh"
+
+BRI_INSTANTIATE_DSLASH(bri::LinkF32<BRI_LINK_FULL>)

@@ -1,0 +1,183 @@
+// The stencil apply (Eq. def_pref, c_SW = 0, in the class form of Sec. 8):
+//
+//   out(x) = (m0 + lambda_0) psi(x)
+//          + sum_{d != 0} s_d(x) [lambda_n + rho_n sum_mu d_mu gamma_mu] (x) W_d(x) psi(x + d)
+//
+// One thread per (site, right-hand side).  The 80 hops are walked as 40 pairs
+// (d, -d) over the stored canonical fields: W_d(x) for the forward hop and
+// W_d(x - d)^dagger for the reversed one.  All offsets, weights and gamma
+// permutations are compile-time constants (the hop loop is a template fold),
+// so each hop is: load W (coalesced 128-bit SoA chunks), load the neighbour
+// spinor, four colour mat-vecs, and the spin combination as real-coefficient
+// accumulations (gamma entries are +-1, +-i).
+//   mode 0: D;  mode 1: D^dagger = gamma_5 D gamma_5 (rho -> -rho, Sec. 1);
+//   mode 2: gamma_5 (D - rho): diagonal -rho + lambda_0, gamma_5 applied to the
+//           result (overlap kernel, Sec. 7.4).
+// Each link format is instantiated in its own translation unit (dslash_*.cu)
+// so the fully unrolled kernels compile in parallel.
+#pragma once
+#include <utility>
+
+#include "ctx.h"
+#include "links.cuh"
+
+namespace bri {
+
+
+BRI_D void load_spinor(const float2 *__restrict__ p, float2 o[12]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        float4 v = q[i];
+        o[2 * i] = make_float2(v.x, v.y);
+        o[2 * i + 1] = make_float2(v.z, v.w);
+    }
+}
+BRI_D void load_spinor(const double2 *__restrict__ p, double2 o[12]) {
+#pragma unroll
+    for (int i = 0; i < 12; i++) o[i] = p[i];
+}
+BRI_D void store_spinor(float2 *__restrict__ p, const float2 o[12]) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 6; i++) q[i] = make_float4(o[2 * i].x, o[2 * i].y, o[2 * i + 1].x, o[2 * i + 1].y);
+}
+BRI_D void store_spinor(double2 *__restrict__ p, const double2 o[12]) {
+#pragma unroll
+    for (int i = 0; i < 12; i++) p[i] = o[i];
+}
+
+template <typename T> struct RealOf;
+template <> struct RealOf<float2> { using R = float; };
+template <> struct RealOf<double2> { using R = double; };
+
+// acc += s * z  and  acc += s * (i z)
+template <typename T, typename R> BRI_D void acc_re(T &acc, R s, T z) {
+    acc.x += s * z.x;
+    acc.y += s * z.y;
+}
+template <typename T, typename R> BRI_D void acc_im(T &acc, R s, T z) {
+    acc.x -= s * z.y;
+    acc.y += s * z.x;
+}
+
+// one hop: offset of hypercube index K, reversed when SGN = -1 (then W is the
+// dagger of the stored field)
+template <int K, int SGN, typename T>
+BRI_D void hop_apply(const M3<T> &W, const T *__restrict__ psi, float ph, float rsign, T acc[12]) {
+    using R = typename RealOf<T>::R;
+    constexpr int n = off_class(K);
+    const R l = (R)lambda_w(n) * (R)ph;
+    const R r = (R)rho_w(n) * (R)(ph * rsign);
+    T p[12];
+    load_spinor(psi, p);
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        T chi[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            T s;
+            if (SGN > 0) {
+                s = cmul(W.e[3 * c], p[3 * sp]);
+                s = cadd(s, cmul(W.e[3 * c + 1], p[3 * sp + 1]));
+                s = cadd(s, cmul(W.e[3 * c + 2], p[3 * sp + 2]));
+            } else {
+                s = cmulc(W.e[c], p[3 * sp]);
+                s = cadd(s, cmulc(W.e[3 + c], p[3 * sp + 1]));
+                s = cadd(s, cmulc(W.e[6 + c], p[3 * sp + 2]));
+            }
+            chi[c] = s;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc_re(acc[3 * sp + c], l, chi[c]);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int dm = SGN * off_comp(K, mu);
+            if (dm == 0) continue;
+            // row s of gamma_mu has its entry in column sp
+            const int s = gcol(mu, sp);
+            const int gr = gre(mu, s), gi = gim(mu, s);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (gr != 0) acc_re(acc[3 * s + c], r * (R)(dm * gr), chi[c]);
+                else acc_im(acc[3 * s + c], r * (R)(dm * gi), chi[c]);
+            }
+        }
+    }
+}
+
+template <int J, class LL>
+BRI_D void hop_pair(const LL &ll, const typename LL::T *__restrict__ in, int site, const SiteNb &nb,
+                    float rsign, typename LL::T acc[12]) {
+    using T = typename LL::T;
+    constexpr int K = canon_k(J);
+    {
+        float ph;
+        const int y = nb_index<K, 1>(nb, site, ph);
+        M3<T> W = ll.load(J, site);
+        hop_apply<K, 1>(W, in + (size_t)y * 12, ph, rsign, acc);
+    }
+    {
+        float ph;
+        const int y = nb_index<K, -1>(nb, site, ph);
+        M3<T> W = ll.load(J, y);
+        hop_apply<K, -1>(W, in + (size_t)y * 12, ph, rsign, acc);
+    }
+}
+
+template <class LL, int... Js>
+BRI_D void all_hops(std::integer_sequence<int, Js...>, const LL &ll, const typename LL::T *__restrict__ in,
+                    int site, const SiteNb &nb, float rsign, typename LL::T acc[12]) {
+    (hop_pair<Js>(ll, in, site, nb, rsign, acc), ...);
+}
+
+template <class LL>
+__global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out, Geom g,
+                         double diag, const int *__restrict__ skip) {
+    using T = typename LL::T;
+    using R = typename RealOf<T>::R;
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= g.V) return;
+    if (skip && skip[blockIdx.y]) return;
+    const size_t off = (size_t)blockIdx.y * g.V * 12;
+    in += off;
+    out += off;
+    int x[4];
+    const SiteNb nb = site_nb(g, site, x);
+    T acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc[i] = mk<T>(0, 0);
+    const float rsign = mode == 1 ? -1.f : 1.f;
+    all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
+    T p[12];
+    load_spinor(in + (size_t)site * 12, p);
+    const R dg = (R)diag;
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        T o;
+        o.x = dg * p[i].x + acc[i].x;
+        o.y = dg * p[i].y + acc[i].y;
+        if (mode == 2 && i >= 6) { o.x = -o.x; o.y = -o.y; }
+        acc[i] = o;
+    }
+    store_spinor(out + (size_t)site * 12, acc);
+}
+
+template <class LL>
+void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
+                   const int *skip, int threads, cudaStream_t s) {
+    using T = typename LL::T;
+    static int max_threads = 0;  // per-kernel limit from its register use
+    if (max_threads == 0) {
+        cudaFuncAttributes attr;
+        max_threads = cudaFuncGetAttributes(&attr, k_dslash<LL>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+    }
+    if (threads > max_threads) threads = max_threads & ~31;
+    dim3 grid((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
+    k_dslash<<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+}
+
+}  // namespace bri
+
+#define BRI_INSTANTIATE_DSLASH(LL) \
+    template void bri::dslash_launch<LL>(int, const LL &, const void *, void *, int, const bri::Geom &, double, const int *, int, cudaStream_t);

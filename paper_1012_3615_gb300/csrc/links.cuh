@@ -1,0 +1,151 @@
+// Storage formats of the 40 hopping fields and their device-side loaders.
+//
+// Every field j is stored structure-of-arrays over sites in 16-byte chunks
+// ([40][chunks][V]), so a warp reading one chunk of 32 consecutive sites issues
+// fully coalesced 128-bit loads:
+//   FP64 full    9 x double2                      144 B
+//   FP32 full    4 x float4 + 1 x float2           72 B
+//   FP32 2-row   3 x float4                        48 B
+//   FP32 8-param 2 x float4                        32 B
+//   FP16 full    2 x uint4 (8 half2) + 1 half2     36 B
+//   FP16 2-row   1 x uint4 + 1 x uint2             24 B
+//   FP16 8-param 1 x uint4                         16 B
+// The reduced forms use that every W_d(x) is in SU(3) (Sec. 5.2): the third row
+// is conj(row0 x row1), and (8-param) U01, U02, U10 with the phases of U00 and
+// U20 fix the rest through unitarity and det = 1:
+//   |U00|^2 = 1 - |U01|^2 - |U02|^2, |U20|^2 = 1 - |U00|^2 - |U10|^2, and with
+//   N = |U01|^2 + |U02|^2, rows 1 and 2 follow from orthogonality to row 0 and
+//   the cofactor identity U^* = cof(U):
+//   (U11, U12) = (U01 a - U02^* b, U02 a + U01^* b) / N, a = -U10 U00^*, b = U20^*
+//   (U21, U22) = (U01 a' - U02^* b', U02 a' + U01^* b') / N, a' = -U20 U00^*, b' = -U10^*
+#pragma once
+#include <cuda_fp16.h>
+
+#include "brillouin.h"
+#include "common.cuh"
+
+namespace bri {
+
+BRI_D float2 h2f(uint32_t u) {
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+
+template <typename T> BRI_D void third_row(M3<T> &m) {
+    m.e[6] = cconj(csub(cmul(m.e[1], m.e[5]), cmul(m.e[2], m.e[4])));
+    m.e[7] = cconj(csub(cmul(m.e[2], m.e[3]), cmul(m.e[0], m.e[5])));
+    m.e[8] = cconj(csub(cmul(m.e[0], m.e[4]), cmul(m.e[1], m.e[3])));
+}
+
+// p = (U01.re, U01.im, U02.re, U02.im, U10.re, U10.im, arg U00, arg U20)
+BRI_D void eight_params(const double2 w[9], float p[8]) {
+    p[0] = (float)w[1].x; p[1] = (float)w[1].y;
+    p[2] = (float)w[2].x; p[3] = (float)w[2].y;
+    p[4] = (float)w[3].x; p[5] = (float)w[3].y;
+    p[6] = (float)atan2(w[0].y, w[0].x);
+    p[7] = (float)atan2(w[6].y, w[6].x);
+}
+
+BRI_D M3<float2> from_eight(const float p[8]) {
+    M3<float2> m;
+    const float2 a1 = make_float2(p[0], p[1]), a2 = make_float2(p[2], p[3]), b0 = make_float2(p[4], p[5]);
+    const float N = a1.x * a1.x + a1.y * a1.y + a2.x * a2.x + a2.y * a2.y;
+    const float r00 = sqrtf(fmaxf(0.f, 1.f - N));
+    float s0, c0, s2, c2;
+    __sincosf(p[6], &s0, &c0);
+    __sincosf(p[7], &s2, &c2);
+    const float2 u00 = make_float2(r00 * c0, r00 * s0);
+    const float r20 = sqrtf(fmaxf(0.f, N - (b0.x * b0.x + b0.y * b0.y)));
+    const float2 u20 = make_float2(r20 * c2, r20 * s2);
+    const float inv = 1.f / N;
+    float2 al = cscale(cmulc(u00, b0), -1.f);  // -U10 U00^*
+    float2 be = cconj(u20);
+    m.e[4] = cscale(csub(cmul(a1, al), cmul(cconj(a2), be)), inv);
+    m.e[5] = cscale(cadd(cmul(a2, al), cmul(cconj(a1), be)), inv);
+    float2 al2 = cscale(cmulc(u00, u20), -1.f);  // -U20 U00^*
+    float2 be2 = cscale(cconj(b0), -1.f);
+    m.e[7] = cscale(csub(cmul(a1, al2), cmul(cconj(a2), be2)), inv);
+    m.e[8] = cscale(cadd(cmul(a2, al2), cmul(cconj(a1), be2)), inv);
+    m.e[0] = u00; m.e[1] = a1; m.e[2] = a2;
+    m.e[3] = b0;  m.e[6] = u20;
+    return m;
+}
+
+struct LinkF64 {
+    using T = double2;
+    const double2 *__restrict__ h;
+    int V;
+    BRI_D M3<double2> load(int j, int site) const {
+        M3<double2> m;
+#pragma unroll
+        for (int e = 0; e < 9; e++) m.e[e] = h[((size_t)j * 9 + e) * V + site];
+        return m;
+    }
+};
+
+template <bri_comp C> struct LinkF32 {
+    using T = float2;
+    const float4 *__restrict__ a;
+    const float2 *__restrict__ b;
+    int V;
+    BRI_D M3<float2> load(int j, int site) const {
+        M3<float2> m;
+        if (C == BRI_LINK_FULL) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                float4 v = a[((size_t)j * 4 + q) * V + site];
+                m.e[2 * q] = make_float2(v.x, v.y);
+                m.e[2 * q + 1] = make_float2(v.z, v.w);
+            }
+            m.e[8] = b[(size_t)j * V + site];
+        } else if (C == BRI_LINK_2ROW) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                float4 v = a[((size_t)j * 3 + q) * V + site];
+                m.e[2 * q] = make_float2(v.x, v.y);
+                m.e[2 * q + 1] = make_float2(v.z, v.w);
+            }
+            third_row(m);
+        } else {
+            float4 v0 = a[((size_t)j * 2) * V + site], v1 = a[((size_t)j * 2 + 1) * V + site];
+            float p[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            m = from_eight(p);
+        }
+        return m;
+    }
+};
+
+template <bri_comp C> struct LinkF16 {
+    using T = float2;
+    const uint4 *__restrict__ a;
+    const void *__restrict__ b;
+    int V;
+    BRI_D M3<float2> load(int j, int site) const {
+        M3<float2> m;
+        if (C == BRI_LINK_FULL) {
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                uint4 v = a[((size_t)j * 2 + q) * V + site];
+                m.e[4 * q] = h2f(v.x);
+                m.e[4 * q + 1] = h2f(v.y);
+                m.e[4 * q + 2] = h2f(v.z);
+                m.e[4 * q + 3] = h2f(v.w);
+            }
+            m.e[8] = h2f(((const uint32_t *)b)[(size_t)j * V + site]);
+        } else if (C == BRI_LINK_2ROW) {
+            uint4 v = a[(size_t)j * V + site];
+            uint2 t = ((const uint2 *)b)[(size_t)j * V + site];
+            m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
+            m.e[4] = h2f(t.x); m.e[5] = h2f(t.y);
+            third_row(m);
+        } else {
+            uint4 v = a[(size_t)j * V + site];
+            float2 q0 = h2f(v.x), q1 = h2f(v.y), q2 = h2f(v.z), q3 = h2f(v.w);
+            float p[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
+            m = from_eight(p);
+        }
+        return m;
+    }
+};
+
+}  // namespace bri

@@ -1,0 +1,249 @@
+// FP64 back-projection to SU(3) (Sec. 5.2, Eq. proj_SU) on the device.
+//
+//   P_SU(3){A} = argmax_{Y in SU(3)} Re tr(A^dagger Y)
+//
+// With A = U S V^dagger, Y = U diag(e^{i theta}) V^dagger and the constraint
+// sum theta_i + phi = 0 (mod 2 pi), e^{i phi} = det A / |det A|, the problem is
+// to maximise sum_i s_i cos(theta_i).  The paper suggests a grid scan and a local
+// maximisation.  Here the stationary points are used directly instead: a
+// Lagrange multiplier kappa gives s_i sin(theta_i) = kappa for every i.  At a
+// maximum only the smallest singular value may have cos(theta) < 0 (swapping
+// phase between two indices would otherwise increase the sum), so the maximum is
+//   branch A: theta_i = asin(kappa / s_i) for all i, when sum_i asin(kappa/s_i)
+//             can reach the target -phi (mod 2 pi) for kappa in [-s_3, s_3];
+//   branch B: theta_3 = pi - asin(kappa / s_3) otherwise.
+// Branch A's sum is strictly increasing in kappa, so its root is unique; the
+// rarely needed branch B is bracketed by a scan.  A (A^dagger A) eigen-
+// decomposition by cyclic complex Jacobi rotations supplies S and V, and
+// Y = A V diag(e^{i theta_i} / s_i) V^dagger.
+#pragma once
+#include "common.cuh"
+
+namespace bri {
+
+// Hermitian 3x3 eigen-decomposition H = V diag(e) V^dagger by Jacobi rotations.
+BRI_D void herm_eig3(double2 H[9], double2 V[9], double e[3]) {
+#pragma unroll
+    for (int i = 0; i < 9; i++) V[i] = make_double2(i % 4 == 0 ? 1.0 : 0.0, 0.0);
+    for (int sweep = 0; sweep < 20; sweep++) {
+        double off = cnorm2(H[1]) + cnorm2(H[2]) + cnorm2(H[5]);
+        double dg = H[0].x * H[0].x + H[4].x * H[4].x + H[8].x * H[8].x;
+        if (off <= 1e-34 * dg || off == 0.0) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; pq++) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            double2 h = H[3 * p + q];
+            double gabs = sqrt(cnorm2(h));
+            if (gabs == 0.0) continue;
+            double a = H[4 * p].x, b = H[4 * q].x;
+            double tau = (b - a) / (2.0 * gabs);
+            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+            double2 ep = make_double2(h.x / gabs, -h.y / gabs);  // e^{-i arg h}
+            double2 se = cscale(ep, s), ce = cscale(ep, c);
+            // H <- H J, V <- V J   (columns p, q)
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                double2 hp = H[3 * i + p], hq = H[3 * i + q];
+                H[3 * i + p] = csub(cscale(hp, c), cmul(hq, se));
+                H[3 * i + q] = cadd(cscale(hp, s), cmul(hq, ce));
+                double2 vp = V[3 * i + p], vq = V[3 * i + q];
+                V[3 * i + p] = csub(cscale(vp, c), cmul(vq, se));
+                V[3 * i + q] = cadd(cscale(vp, s), cmul(vq, ce));
+            }
+            // H <- J^dagger H   (rows p, q)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double2 hp = H[3 * p + j], hq = H[3 * q + j];
+                H[3 * p + j] = csub(cscale(hp, c), cmul(cconj(se), hq));
+                H[3 * q + j] = cadd(cscale(hp, s), cmul(cconj(ce), hq));
+            }
+            H[3 * p + q] = make_double2(0, 0);
+            H[3 * q + p] = make_double2(0, 0);
+            H[4 * p].y = 0;
+            H[4 * q].y = 0;
+        }
+    }
+    e[0] = H[0].x;
+    e[1] = H[4].x;
+    e[2] = H[8].x;
+}
+
+// sum_i asin(kappa/s_i) - t and its derivative
+BRI_D double branch_a(const double s[3], double kappa, double t, double &deriv) {
+    double f = -t, d = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double r = kappa / s[i];
+        r = fmin(1.0, fmax(-1.0, r));
+        f += asin(r);
+        d += 1.0 / sqrt(fmax(s[i] * s[i] - kappa * kappa, 1e-300));
+    }
+    deriv = d;
+    return f;
+}
+
+// root of branch A for target t, |t| <= M guaranteed by the caller
+BRI_D double solve_branch_a(const double s[3], double t) {
+    double lo = -s[2], hi = s[2];
+    double kappa = t / (1.0 / s[0] + 1.0 / s[1] + 1.0 / s[2]);
+    kappa = fmin(hi, fmax(lo, kappa));
+    for (int it = 0; it < 200; it++) {
+        double d;
+        double f = branch_a(s, kappa, t, d);
+        if (f == 0.0) break;
+        if (f > 0) hi = kappa; else lo = kappa;
+        double kn = kappa - f / d;
+        if (!(kn > lo && kn < hi)) kn = 0.5 * (lo + hi);
+        if (fabs(kn - kappa) <= 2e-16 * s[2] || hi - lo <= 2e-16 * s[2]) { kappa = kn; break; }
+        kappa = kn;
+    }
+    return kappa;
+}
+
+BRI_D double branch_b(const double s[3], double kappa, double t) {
+    double r0 = fmin(1.0, fmax(-1.0, kappa / s[0]));
+    double r1 = fmin(1.0, fmax(-1.0, kappa / s[1]));
+    double r2 = fmin(1.0, fmax(-1.0, kappa / s[2]));
+    return asin(r0) + asin(r1) + 3.14159265358979323846 - asin(r2) - t;
+}
+
+// maximiser of s1 cos t1 + s2 cos t2 + s3 cos t3 with t1+t2+t3 = -phi (mod 2 pi);
+// s must be sorted descending and positive.
+BRI_D void phase_solve(const double s[3], double phi, double th[3]) {
+    const double PI = 3.14159265358979323846;
+    const double c = -phi;
+    const double M = asin(fmin(1.0, s[2] / s[0])) + asin(fmin(1.0, s[2] / s[1])) + 0.5 * PI;
+    double best = -1e300;
+    bool found = false;
+    for (int rep = -1; rep <= 1; rep++) {
+        double t = c + 2.0 * PI * rep;
+        if (fabs(t) > M) continue;
+        double kappa = solve_branch_a(s, t);
+        double f = 0, tt[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            tt[i] = asin(fmin(1.0, fmax(-1.0, kappa / s[i])));
+            f += sqrt(fmax(s[i] * s[i] - kappa * kappa, 0.0));
+        }
+        // place the rounding residue of the constraint on theta_3
+        tt[2] = t - tt[0] - tt[1];
+        if (f > best) {
+            best = f;
+            found = true;
+            th[0] = tt[0]; th[1] = tt[1]; th[2] = tt[2];
+        }
+    }
+    if (found) return;
+    // branch B: theta_3 = pi - asin(kappa/s_3); the target lies in (M, 2 pi - M)
+    double t = c < 0 ? c + 2.0 * PI : c;
+    const int NS = 64;
+    double prevk = -s[2], prevg = branch_b(s, prevk, t);
+    for (int i = 1; i <= NS; i++) {
+        double k = -s[2] + 2.0 * s[2] * i / NS;
+        double g = branch_b(s, k, t);
+        if (prevg == 0.0 || (prevg < 0) != (g < 0)) {
+            double lo = prevk, hi = k, glo = prevg;
+            for (int it = 0; it < 80; it++) {
+                double mid = 0.5 * (lo + hi);
+                double gm = branch_b(s, mid, t);
+                if ((gm < 0) == (glo < 0)) { lo = mid; glo = gm; } else hi = mid;
+            }
+            double kappa = 0.5 * (lo + hi);
+            double t0 = asin(fmin(1.0, fmax(-1.0, kappa / s[0])));
+            double t1 = asin(fmin(1.0, fmax(-1.0, kappa / s[1])));
+            double t2 = t - t0 - t1;
+            double f = s[0] * cos(t0) + s[1] * cos(t1) + s[2] * cos(t2);
+            if (f > best) { best = f; th[0] = t0; th[1] = t1; th[2] = t2; }
+        }
+        prevk = k;
+        prevg = g;
+    }
+}
+
+BRI_D double2 det3(const double2 A[9]) {
+    double2 m0 = csub(cmul(A[4], A[8]), cmul(A[5], A[7]));
+    double2 m1 = csub(cmul(A[3], A[8]), cmul(A[5], A[6]));
+    double2 m2 = csub(cmul(A[3], A[7]), cmul(A[4], A[6]));
+    return cadd(csub(cmul(A[0], m0), cmul(A[1], m1)), cmul(A[2], m2));
+}
+
+// singular basis and phases of a projection (for its derivative)
+struct ProjectionParts {
+    double2 V[9];
+    double s[3], th[3];
+};
+
+BRI_D M3<double2> project_su3(const M3<double2> &A, ProjectionParts *parts = nullptr) {
+    double2 H[9], V[9];
+    double e[3];
+    // H = A^dagger A
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            double2 sum = make_double2(0, 0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) sum = cadd(sum, cmulc(A.e[3 * k + i], A.e[3 * k + j]));
+            H[3 * i + j] = sum;
+        }
+    herm_eig3(H, V, e);
+    // sort eigenpairs descending
+    int o[3] = {0, 1, 2};
+    if (e[o[0]] < e[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    if (e[o[1]] < e[o[2]]) { int t = o[1]; o[1] = o[2]; o[2] = t; }
+    if (e[o[0]] < e[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    double s[3];
+    double2 Vs[9];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        s[k] = sqrt(fmax(e[o[k]], 0.0));
+#pragma unroll
+        for (int i = 0; i < 3; i++) Vs[3 * i + k] = V[3 * i + o[k]];
+    }
+    const double tiny = 1e-300;
+    s[2] = fmax(s[2], tiny);
+    s[1] = fmax(s[1], tiny);
+    s[0] = fmax(s[0], tiny);
+    double2 d = det3(A.e);
+    double phi = atan2(d.y, d.x);
+    double th[3];
+    phase_solve(s, phi, th);
+    if (parts) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) parts->V[i] = Vs[i];
+#pragma unroll
+        for (int k = 0; k < 3; k++) { parts->s[k] = s[k]; parts->th[k] = th[k]; }
+    }
+    // Y = A V diag(e^{i th}/s) V^dagger
+    double2 ph[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        double sn, cs;
+        sincos(th[k], &sn, &cs);
+        ph[k] = make_double2(cs / s[k], sn / s[k]);
+    }
+    double2 B[9];  // V diag(ph) V^dagger
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            double2 sum = make_double2(0, 0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) sum = cadd(sum, cmul(cmul(Vs[3 * i + k], ph[k]), cconj(Vs[3 * j + k])));
+            B[3 * i + j] = sum;
+        }
+    M3<double2> Y;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            double2 sum = make_double2(0, 0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) sum = cadd(sum, cmul(A.e[3 * i + k], B[3 * k + j]));
+            Y.e[3 * i + j] = sum;
+        }
+    return Y;
+}
+
+}  // namespace bri

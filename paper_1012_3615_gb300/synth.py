@@ -120,3 +120,37 @@ def plane_wave(L, k, u):
     x = coordinates(L)
     ph = np.exp(1j * (x @ np.asarray(k, dtype=np.float64)))
     return np.ascontiguousarray(ph[:, None, None] * np.asarray(u, np.complex128)[None])
+
+
+def random_su3_links_torch(L, eps, seed, device="cuda", chunk=1 << 20):
+    """Same distribution as random_su3_links, drawn with torch on the device
+    (for lattices too large to generate on the host in reasonable time; the
+    random stream differs from the numpy one)."""
+    import torch
+
+    V = volume(L)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lam = torch.as_tensor(_gell_mann(), device=device)
+    U = torch.empty((V * 4, 3, 3), dtype=torch.complex128, device=device)
+    for s in range(0, V * 4, chunk):
+        e = min(V * 4, s + chunk)
+        h = torch.randn((e - s, 8), generator=g, dtype=torch.float64, device=device)
+        H = torch.einsum("na,aij->nij", h.to(torch.complex128), lam) / 2.0
+        M = torch.linalg.matrix_exp(1j * eps * H)
+        det = torch.linalg.det(M)
+        U[s:e] = M / (det ** (1.0 / 3.0))[:, None, None]
+    return U.reshape(V, 4, 3, 3)
+
+
+def gaussian_spinor_torch(L, nrhs, seed, device="cuda", dtype=None):
+    import torch
+
+    dtype = dtype or torch.complex128
+    V = volume(L)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rdt = torch.float64 if dtype == torch.complex128 else torch.float32
+    re = torch.randn((nrhs, V, 4, 3), generator=g, dtype=rdt, device=device)
+    im = torch.randn((nrhs, V, 4, 3), generator=g, dtype=rdt, device=device)
+    return torch.complex(re, im) / 2 ** 0.5

@@ -1,0 +1,177 @@
+"""GPU stencil apply (Eq. def_pref, class form of Sec. 8) against the CPU
+oracle: FP64 to 1e-13 relative, FP32 to 1e-6, per link storage format, for
+D, D^dagger and the overlap kernel gamma_5 (D - rho)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1012_3615_gb300 import Brillouin, BriError, synth
+
+pytestmark = pytest.mark.gpu
+AP = (1, 1, 1, -1)
+PER = (1, 1, 1, 1)
+
+CASES = [((4, 4, 4, 4), AP), ((3, 5, 4, 6), AP), ((4, 3, 3, 4), PER), ((3, 3, 3, 3), AP)]
+
+
+def _setup(L, bc, seed, nrhs=2, eps=0.4):
+    U = synth.random_su3_links(L, eps, seed)
+    psi = synth.gaussian_spinor(L, nrhs, seed + 1)
+    W = oracle.build_hops(L, U)
+    return U, psi, W
+
+
+def _rel_max(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("L,bc", CASES)
+def test_fp64_apply_dagger_overlap(gpu, L, bc):
+    U, psi, W = _setup(L, bc, sum(L))
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu))
+    x = torch.as_tensor(psi, device=gpu)
+    m0 = -0.07
+    out = op.apply(x, m0=m0).cpu().numpy()
+    outd = op.apply(x, m0=m0, dagger=True).cpu().numpy()
+    outh = op.overlap_kernel(x, rho=1.0).cpu().numpy()
+    for r in range(psi.shape[0]):
+        assert _rel_max(out[r], oracle.apply(L, bc, W, m0, psi[r])) < 1e-13
+        assert _rel_max(outd[r], oracle.apply(L, bc, W, m0, psi[r], dagger=True)) < 1e-13
+        assert _rel_max(outh[r], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) < 1e-13
+
+
+@pytest.mark.parametrize("comp,tol", [("full", 1e-6), ("2row", 1e-6), ("8param", 2e-5)])
+@pytest.mark.parametrize("L,bc", CASES[:2])
+def test_fp32_apply(gpu, L, bc, comp, tol):
+    U, psi, W = _setup(L, bc, 10 + sum(L))
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp=comp)
+    x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
+    for dag in (False, True):
+        out = op.apply(x, m0=0.02, dagger=dag, prec="f32").cpu().numpy()
+        for r in range(psi.shape[0]):
+            ref = oracle.apply(L, bc, W, 0.02, psi[r], dagger=dag)
+            assert _rel_l2(out[r], ref) < tol
+    outh = op.overlap_kernel(x, rho=1.0, prec="f32").cpu().numpy()
+    assert _rel_l2(outh[0], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[0])) < tol
+
+
+@pytest.mark.parametrize("comp,tol", [("full", 2e-3), ("2row", 2e-3), ("8param", 1e-2)])
+def test_fp16_links_apply(gpu, comp, tol):
+    L, bc = (4, 4, 4, 6), AP
+    U, psi, W = _setup(L, bc, 21)
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f16", comp=comp)
+    x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
+    out = op.apply(x, m0=0.0, prec="f16").cpu().numpy()
+    for r in range(psi.shape[0]):
+        assert _rel_l2(out[r], oracle.apply(L, bc, W, 0.0, psi[r])) < tol
+
+
+def test_multi_rhs_equals_single(gpu):
+    L, bc = (4, 3, 5, 4), AP
+    U = synth.random_su3_links(L, 0.3, 5)
+    psi = synth.gaussian_spinor(L, 24, 6)
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp="2row")
+    for prec, dt in (("f64", np.complex128), ("f32", np.complex64)):
+        x = torch.as_tensor(psi.astype(dt), device=gpu)
+        many = op.apply(x, 0.1, prec=prec)
+        for r in (0, 7, 23):
+            one = op.apply(x[r:r + 1].contiguous(), 0.1, prec=prec)
+            assert torch.equal(many[r:r + 1], one)
+
+
+def test_free_field_plane_wave_on_gpu(gpu):
+    """U = 1: D acts on exp(i k.x) u as the momentum-space symbol built from
+    the closed forms of Eq. def_4Dbri and App. C (no oracle involved)."""
+    L, bc = (8, 8, 6, 12), AP
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(synth.unit_links(L), device=gpu))
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        k = [2 * np.pi * rng.integers(0, L[m]) / L[m] for m in range(3)] + \
+            [(2 * rng.integers(0, L[3]) + 1) * np.pi / L[3]]
+        k = np.array(k)
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        psi = synth.plane_wave(L, k, u)
+        out = op.apply(torch.as_tensor(psi, device=gpu), m0=0.3).cpu().numpy()
+        M = (0.3 + 2 - 2 * np.prod(np.cos(k / 2) ** 2)) * np.eye(4, dtype=complex)
+        for mu in range(4):
+            M = M + 1j * np.sin(k[mu]) * np.prod([np.cos(k[nu]) + 2 for nu in range(4) if nu != mu]) / 27 \
+                * oracle.gamma(mu)
+        expect = synth.plane_wave(L, k, M @ u)
+        assert _rel_max(out, expect) < 1e-13
+
+
+def test_gauge_covariance_and_gamma5_hermiticity_on_gpu(gpu):
+    L, bc = (6, 6, 6, 8), AP
+    U = synth.random_su3_links(L, 0.4, 8)
+    g = synth.gauge_transform(L, 9)
+    x = synth.coordinates(L)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        y = x.copy()
+        y[:, mu] = (y[:, mu] + 1) % L[mu]
+        yi = y[:, 0] + L[0] * (y[:, 1] + L[1] * (y[:, 2] + L[2] * y[:, 3]))
+        Ug[:, mu] = g @ U[:, mu] @ g[yi].conj().transpose(0, 2, 1)
+    psi, phi = synth.gaussian_spinor(L, 2, 10)
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu))
+    Dpsi = op.apply(torch.as_tensor(psi, device=gpu), -0.1).cpu().numpy()
+    Ddphi = op.apply(torch.as_tensor(phi, device=gpu), -0.1, dagger=True).cpu().numpy()
+    assert abs(np.vdot(phi, Dpsi) - np.vdot(Ddphi, psi)) < 1e-10 * abs(np.vdot(phi, Dpsi))
+    op.build_hops(torch.as_tensor(Ug, device=gpu))
+    gpsi = np.einsum("xab,xsb->xsa", g, psi)
+    lhs = op.apply(torch.as_tensor(gpsi, device=gpu), -0.1).cpu().numpy()
+    assert _rel_max(lhs, np.einsum("xab,xsb->xsa", g, Dpsi)) < 1e-12
+
+
+def test_full_size_sampled_sites(gpu):
+    """32^3 x 64 in the benchmark's launch configuration (FP32 full links,
+    tuned block size) and in FP64: sampled output sites against the oracle,
+    which builds the hops of each sampled site from U on the spot."""
+    L, bc = (32, 32, 32, 64), AP
+    U = synth.random_su3_links_torch(L, 0.3, 1015, device=gpu)
+    psi = synth.gaussian_spinor_torch(L, 1, 1016, device=gpu)
+    op = Brillouin(L, bc)
+    op.build_hops(U, prec="f32", comp="full")
+    op.tune("f32", 1)
+    out64 = op.apply(psi, 0.0, prec="f64")
+    out32 = op.apply(psi.to(torch.complex64), 0.0, prec="f32")
+    rng = np.random.default_rng(11)
+    V = synth.volume(L)
+    sites = np.concatenate([[0, V - 1, 31, V - 32 * 32 * 32], rng.integers(0, V, 6)])
+    Uh = U.cpu().numpy()
+    ph = psi[0].cpu().numpy()
+    ref = oracle.apply_sites(L, bc, Uh, 0.0, ph, sites)
+    g64 = out64[0].cpu().numpy()[sites]
+    g32 = out32[0].cpu().numpy()[sites]
+    assert _rel_max(g64, ref) < 1e-13
+    assert _rel_l2(g32, ref) < 1e-6
+    del op
+    torch.cuda.empty_cache()
+
+
+def test_argument_errors(gpu):
+    L = (3, 3, 3, 3)
+    op = Brillouin(L, AP)
+    x = torch.zeros((1, 81, 4, 3), dtype=torch.complex128, device=gpu)
+    with pytest.raises(BriError, match="BRI_ESTATE"):
+        op.apply(x)  # no hops yet
+    op.build_hops(torch.as_tensor(synth.unit_links(L), device=gpu))
+    with pytest.raises(BriError, match="BRI_ESTATE"):
+        op.apply(x.to(torch.complex64), prec="f32")  # FP32 fields not stored
+    with pytest.raises(BriError, match="BRI_EINVAL"):
+        op.apply(x, out=x)  # in-place
+    big = torch.zeros(81 * 12 + 1, dtype=torch.complex64, device=gpu)
+    with pytest.raises(BriError, match="BRI_EINVAL"):
+        op.apply(big[1:].view(1, 81, 4, 3), prec="f32")  # 8-byte offset: not 16-byte aligned
+    with pytest.raises(BriError):
+        Brillouin((2, 4, 4, 4))

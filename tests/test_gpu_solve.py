@@ -1,0 +1,88 @@
+"""GPU BiCGstab (Sec. 6.4): FP64, mixed-precision defect correction and the
+batched multi-RHS solve, all to a true FP64 residual of 1e-10, plus the
+failure statuses (non-convergence, NaN, zero source)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1012_3615_gb300 import Brillouin, synth
+
+pytestmark = pytest.mark.gpu
+AP = (1, 1, 1, -1)
+
+
+def _true_resid(L, bc, W, m0, x, b):
+    r = b - oracle.apply(L, bc, W, m0, x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def test_fp64_solve_matches_oracle(gpu):
+    L = (4, 4, 4, 4)
+    U = synth.random_su3_links(L, 0.4, 1)
+    b = synth.z2_spinor(L, 1, 2)
+    W = oracle.build_hops(L, U)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu))
+    x, info = op.solve(torch.as_tensor(b, device=gpu), m0=-0.05, tol=1e-10, mode=0)
+    assert info[0]["status"] == "BRI_OK", info
+    x = x.cpu().numpy()[0]
+    assert _true_resid(L, AP, W, -0.05, x, b[0]) <= 1e-10
+    xo, st, it, tr = oracle.bicgstab(L, AP, W, -0.05, b[0], tol=1e-12)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-8
+
+
+@pytest.mark.parametrize("mode,comp", [(1, "2row"), (2, "2row"), (1, "full"), (2, "full")])
+def test_mixed_precision_solves(gpu, mode, comp):
+    L = (4, 4, 4, 6)
+    U = synth.random_su3_links(L, 0.4, 3)
+    b = synth.z2_spinor(L, 1, 4)
+    W = oracle.build_hops(L, U)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32" if mode == 1 else "f16", comp=comp)
+    x, info = op.solve(torch.as_tensor(b, device=gpu), m0=-0.05, tol=1e-10, mode=mode)
+    assert info[0]["status"] == "BRI_OK", info
+    assert info[0]["outer_iters"] >= 1
+    assert _true_resid(L, AP, W, -0.05, x.cpu().numpy()[0], b[0]) <= 1e-10
+
+
+def test_batched_point_sources(gpu):
+    L = (4, 4, 4, 4)
+    U = synth.random_su3_links(L, 0.35, 5)
+    b, x0 = synth.point_sources(L, 6)
+    W = oracle.build_hops(L, U)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f16", comp="2row")
+    x, info = op.solve(torch.as_tensor(b, device=gpu), m0=0.0, tol=1e-10, mode=3)
+    assert all(i["status"] == "BRI_OK" for i in info), info
+    xs = x.cpu().numpy()
+    for r in range(12):
+        assert _true_resid(L, AP, W, 0.0, xs[r], b[r]) <= 1e-10
+    x0s, info0 = op.solve(torch.as_tensor(b[:2], device=gpu), m0=0.0, tol=1e-12, mode=0)
+    assert np.linalg.norm(xs[:2] - x0s.cpu().numpy()) / np.linalg.norm(x0s.cpu().numpy()) < 1e-8
+
+
+def test_singular_operator_reports_nonconvergence(gpu):
+    L = (4, 4, 4, 4)
+    op = Brillouin(L, (1, 1, 1, 1))
+    op.build_hops(torch.as_tensor(synth.unit_links(L), device=gpu))
+    b = torch.ones((1, 256, 4, 3), dtype=torch.complex128, device=gpu)
+    x, info = op.solve(b, m0=0.0, tol=1e-10, maxit=40, mode=0)
+    assert info[0]["status"] != "BRI_OK"
+    assert info[0]["iters"] <= 40 + 8
+
+
+def test_nan_and_zero_sources(gpu):
+    L = (3, 3, 3, 4)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(synth.random_su3_links(L, 0.3, 7), device=gpu), prec="f32", comp="2row")
+    b = torch.as_tensor(synth.gaussian_spinor(L, 1, 8), device=gpu)
+    b[0, 5, 1, 2] = float("nan")
+    for mode in (0, 1):
+        x, info = op.solve(b, m0=0.0, mode=mode)
+        assert info[0]["status"] == "BRI_ENAN", (mode, info)
+    z = torch.zeros_like(b)
+    for mode in (0, 1):
+        x, info = op.solve(z, m0=0.0, mode=mode)
+        assert info[0]["status"] == "BRI_OK"
+        assert torch.count_nonzero(x) == 0
