@@ -16,13 +16,14 @@ Parity unpinned: nothing -- every function is pinned by tests/test_oracle_*.py.
 """
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "brillouin_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+_BUILD = os.path.join(_HERE, "_build", platform.machine())
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 

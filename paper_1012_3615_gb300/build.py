@@ -7,6 +7,7 @@ unit per hopping-field format so the fully unrolled kernels build in parallel.
 """
 import glob
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -14,7 +15,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# one build directory per host architecture: objects never mix across machines
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(BUILD, "libbrillouin.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

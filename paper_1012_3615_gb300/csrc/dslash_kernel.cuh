@@ -61,11 +61,76 @@ template <typename T, typename R> BRI_D void acc_im(T &acc, R s, T z) {
     acc.y += s * z.x;
 }
 
+// Accumulators.  FP32: the terms with a real gamma entry go to a, those with
+// an imaginary entry (+-i) to ai, and out = a + i ai at the end, so every
+// accumulation is a real-coefficient packed FMA (fma.rn.f32x2 on sm_103a: two
+// FP32 FMAs per instruction, halving the issue slots of the arithmetic).
+struct AccF {
+    float2 a[12], ai[12];
+};
+struct AccD {
+    double2 a[12];
+};
+template <typename T> struct AccOf;
+template <> struct AccOf<float2> { using A = AccF; };
+template <> struct AccOf<double2> { using A = AccD; };
+
+BRI_D float2 f2(float v) { return make_float2(v, v); }
+
+// FP32 hop with packed FMAs: chi = W psi as sum_c' (psi.re * w + psi.im * (i w))
+template <int K, int SGN>
+BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, AccF &acc) {
+    constexpr int n = off_class(K);
+    const float l = (float)lambda_w(n) * ph;
+    const float r = (float)rho_w(n) * (ph * rsign);
+    float2 A[9], B[9];  // matrix entries w and i w (w = W or W^dagger entry)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) {
+            const float2 w = SGN > 0 ? W.e[3 * c + cp] : make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
+            A[3 * c + cp] = w;
+            B[3 * c + cp] = make_float2(-w.y, w.x);
+        }
+    float2 p[12];
+    load_spinor(psi, p);
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        float2 chi[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
+            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
+            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
+            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
+            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
+            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
+            chi[c] = t;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc.a[3 * sp + c] = __ffma2_rn(f2(l), chi[c], acc.a[3 * sp + c]);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int dm = SGN * off_comp(K, mu);
+            if (dm == 0) continue;
+            const int s = gcol(mu, sp);
+            const int gr = gre(mu, s), gi = gim(mu, s);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(r * (float)(dm * gr)), chi[c], acc.a[3 * s + c]);
+                else acc.ai[3 * s + c] = __ffma2_rn(f2(r * (float)(dm * gi)), chi[c], acc.ai[3 * s + c]);
+            }
+        }
+    }
+}
+
 // one hop: offset of hypercube index K, reversed when SGN = -1 (then W is the
 // dagger of the stored field)
-template <int K, int SGN, typename T>
-BRI_D void hop_apply(const M3<T> &W, const T *__restrict__ psi, float ph, float rsign, T acc[12]) {
-    using R = typename RealOf<T>::R;
+template <int K, int SGN>
+BRI_D void hop_apply(const M3<double2> &W, const double2 *__restrict__ psi, float ph, float rsign, AccD &accd) {
+    using T = double2;
+    using R = double;
+    T *acc = accd.a;
     constexpr int n = off_class(K);
     const R l = (R)lambda_w(n) * (R)ph;
     const R r = (R)rho_w(n) * (R)(ph * rsign);
@@ -108,7 +173,7 @@ BRI_D void hop_apply(const M3<T> &W, const T *__restrict__ psi, float ph, float 
 
 template <int J, class LL>
 BRI_D void hop_pair(const LL &ll, const typename LL::T *__restrict__ in, int site, const SiteNb &nb,
-                    float rsign, typename LL::T acc[12]) {
+                    float rsign, typename AccOf<typename LL::T>::A &acc) {
     using T = typename LL::T;
     constexpr int K = canon_k(J);
     {
@@ -127,7 +192,7 @@ BRI_D void hop_pair(const LL &ll, const typename LL::T *__restrict__ in, int sit
 
 template <class LL, int... Js>
 BRI_D void all_hops(std::integer_sequence<int, Js...>, const LL &ll, const typename LL::T *__restrict__ in,
-                    int site, const SiteNb &nb, float rsign, typename LL::T acc[12]) {
+                    int site, const SiteNb &nb, float rsign, typename AccOf<typename LL::T>::A &acc) {
     (hop_pair<Js>(ll, in, site, nb, rsign, acc), ...);
 }
 
@@ -144,23 +209,32 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
     out += off;
     int x[4];
     const SiteNb nb = site_nb(g, site, x);
-    T acc[12];
+    typename AccOf<T>::A acc;
 #pragma unroll
-    for (int i = 0; i < 12; i++) acc[i] = mk<T>(0, 0);
+    for (int i = 0; i < 12; i++) acc.a[i] = mk<T>(0, 0);
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int i = 0; i < 12; i++) acc.ai[i] = mk<T>(0, 0);
+    }
     const float rsign = mode == 1 ? -1.f : 1.f;
     all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
     T p[12];
     load_spinor(in + (size_t)site * 12, p);
     const R dg = (R)diag;
+    T o[12];
 #pragma unroll
     for (int i = 0; i < 12; i++) {
-        T o;
-        o.x = dg * p[i].x + acc[i].x;
-        o.y = dg * p[i].y + acc[i].y;
-        if (mode == 2 && i >= 6) { o.x = -o.x; o.y = -o.y; }
-        acc[i] = o;
+        T v;
+        v.x = dg * p[i].x + acc.a[i].x;
+        v.y = dg * p[i].y + acc.a[i].y;
+        if constexpr (sizeof(T) == 8) {
+            v.x -= acc.ai[i].y;
+            v.y += acc.ai[i].x;
+        }
+        if (mode == 2 && i >= 6) { v.x = -v.x; v.y = -v.y; }
+        o[i] = v;
     }
-    store_spinor(out + (size_t)site * 12, acc);
+    store_spinor(out + (size_t)site * 12, o);
 }
 
 template <class LL>
