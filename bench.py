@@ -231,7 +231,7 @@ def native(args, world, rank, local, pg):
     dev = torch.device("cuda", local)
     mode, nrhs = args.mode, args.nrhs
     prec, comp = mode.split("-")
-    L = L_BENCH
+    L = tuple(args.lattice) if args.lattice else L_BENCH
     V = synth.volume(L)
     U = synth.random_su3_links_torch(L, EPS, SEED + rank, device=dev)
     op = Brillouin(L, BC)
@@ -240,7 +240,10 @@ def native(args, world, rank, local, pg):
     sdt = torch.complex128 if prec == "f64" else torch.complex64
     x = synth.gaussian_spinor_torch(L, nrhs, SEED + 100 + rank, device=dev, dtype=sdt)
     out = torch.empty_like(x)
-    op.tune(prec, nrhs)
+    if args.threads:
+        op.set_threads(prec, nrhs, args.threads)
+    else:
+        op.tune(prec, nrhs)
     stream = torch.cuda.current_stream()
     time_apply(op, x, out, mode, nrhs, 1, args.warmup, stream)  # warm-up (untimed)
 
@@ -291,8 +294,9 @@ def native(args, world, rank, local, pg):
         "metric": "D_B apply GB/s", "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
-        "config": {"workload": "D_B apply, 32^3x64 lattice, antiperiodic t, links exp(i0.3H), Gaussian spinors",
-                   "lattice": list(L), "nrhs": nrhs, "hop_storage": mode, "threads_per_block": None,
+        "config": {"workload": "D_B apply, %s lattice, antiperiodic t, links exp(i0.3H), Gaussian spinors"
+                               % "x".join(str(v) for v in L),
+                   "lattice": list(L), "nrhs": nrhs, "hop_storage": mode, "threads_per_block": op.threads(prec, nrhs),
                    "l2": "inputs larger than L2 (hopping fields %.1f GB)" % (LINK_BYTES[mode] * V / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": dslash_gbs, "peak": peak, "unit": "GB/s",
@@ -340,6 +344,9 @@ def main():
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--lattice", type=lambda t: [int(v) for v in t.split(",")], default=None,
+                    help="lattice extents x,y,z,t (default 32,32,32,64)")
+    ap.add_argument("--threads", type=int, default=0, help="fixed threads per block (skips the tuner)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local, pg = dist_setup(args)

@@ -177,6 +177,13 @@ bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, voi
  * Requires the fields of that precision.  Synchronises the stream. */
 bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
 
+/* Set / read the threads per block of the apply kernels for (prec, nrhs)
+ * (what bri_tune chooses; 0 < threads <= 1024, rounded down to a multiple of
+ * 32 and clamped to the kernel's limit at launch).  bri_get_threads returns
+ * the current choice (128 when untuned) or a negative bri_status. */
+bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
+int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
+
 /* Number of kernels this context launched so far (diagnostics). */
 long bri_kernel_launches(bri_ctx *ctx);
 

@@ -48,6 +48,8 @@ SIGNATURES = {
                                   ctypes.POINTER(bri_solve_info), c_void_p]),
     "bri_project_su3": (c_int, [c_void_p, c_void_p, c_void_p, c_long, c_void_p]),
     "bri_tune": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "bri_set_threads": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "bri_get_threads": (c_int, [c_void_p, c_int, c_int]),
     "bri_kernel_launches": (c_long, [c_void_p]),
     "bri_last_error": (ctypes.c_char_p, [c_void_p]),
 }

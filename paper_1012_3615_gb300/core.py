@@ -132,5 +132,14 @@ class Brillouin:
     def tune(self, prec="f32", nrhs=1):
         self._check(self.lib.bri_tune(self.ctx, _PREC[prec], int(nrhs), _stream()))
 
+    def set_threads(self, prec, nrhs, threads):
+        self._check(self.lib.bri_set_threads(self.ctx, _PREC[prec], int(nrhs), int(threads)))
+
+    def threads(self, prec, nrhs=1):
+        t = self.lib.bri_get_threads(self.ctx, _PREC[prec], int(nrhs))
+        if t < 0:
+            self._check(t)
+        return t
+
     def kernel_launches(self):
         return int(self.lib.bri_kernel_launches(self.ctx))

@@ -231,6 +231,20 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream) {
     return bri_tune_impl(ctx, prec, nrhs, as_stream(stream));
 }
 
+bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    if (nrhs < 1 || threads < 32 || threads > 1024) return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
+    ctx->tune[bri_tune_key(ctx, prec, nrhs)] = threads & ~31;
+    return BRI_OK;
+}
+
+int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
+    if (!ctx) return BRI_EINVAL;
+    if (check_prec(ctx, prec) != BRI_OK || nrhs < 1) return BRI_EINVAL;
+    return bri_dslash_threads(ctx, prec, nrhs);
+}
+
 long bri_kernel_launches(bri_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 const char *bri_last_error(bri_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }

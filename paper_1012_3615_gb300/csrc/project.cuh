@@ -15,7 +15,7 @@
 // Branch A's sum is strictly increasing in kappa, so its root is unique; the
 // rarely needed branch B is bracketed by a scan.  A (A^dagger A) eigen-
 // decomposition by cyclic complex Jacobi rotations supplies S and V, and
-// Y = A V diag(e^{i theta_i} / s_i) V^dagger.
+// Y = U diag(e^{i theta_i}) V^dagger with U = A V S^{-1}.
 #pragma once
 #include "common.cuh"
 
@@ -161,6 +161,14 @@ BRI_D void phase_solve(const double s[3], double phi, double th[3]) {
     }
 }
 
+BRI_D void swap_cols(double2 U[9], double2 V[9], int a, int b) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double2 t = U[3 * i + a]; U[3 * i + a] = U[3 * i + b]; U[3 * i + b] = t;
+        t = V[3 * i + a]; V[3 * i + a] = V[3 * i + b]; V[3 * i + b] = t;
+    }
+}
+
 BRI_D double2 det3(const double2 A[9]) {
     double2 m0 = csub(cmul(A[4], A[8]), cmul(A[5], A[7]));
     double2 m1 = csub(cmul(A[3], A[8]), cmul(A[5], A[6]));
@@ -193,20 +201,55 @@ BRI_D M3<double2> project_su3(const M3<double2> &A, ProjectionParts *parts = nul
     if (e[o[0]] < e[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
     if (e[o[1]] < e[o[2]]) { int t = o[1]; o[1] = o[2]; o[2] = t; }
     if (e[o[0]] < e[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
-    double s[3];
     double2 Vs[9];
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        s[k] = sqrt(fmax(e[o[k]], 0.0));
+    for (int k = 0; k < 3; k++)
 #pragma unroll
         for (int i = 0; i < 3; i++) Vs[3 * i + k] = V[3 * i + o[k]];
-    }
+    // U = A V S^{-1}: the columns of A V are orthogonal with norms s_k.  Taking s_k
+    // as those column norms (not as square roots of the eigenvalues of A^dagger A)
+    // keeps small singular values accurate; one Gram-Schmidt pass removes the
+    // residual non-orthogonality.
+    double2 Um[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            double2 sum = make_double2(0, 0);
+#pragma unroll
+            for (int l = 0; l < 3; l++) sum = cadd(sum, cmul(A.e[3 * i + l], Vs[3 * l + k]));
+            Um[3 * i + k] = sum;
+        }
+    double s[3];
     const double tiny = 1e-300;
-    s[2] = fmax(s[2], tiny);
-    s[1] = fmax(s[1], tiny);
-    s[0] = fmax(s[0], tiny);
-    double2 d = det3(A.e);
-    double phi = atan2(d.y, d.x);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        // remove the components along the previous (orthonormal) columns
+#pragma unroll
+        for (int q = 0; q < k; q++) {
+            double2 dot = make_double2(0, 0);
+#pragma unroll
+            for (int i = 0; i < 3; i++) dot = cadd(dot, cmulc(Um[3 * i + q], Um[3 * i + k]));
+#pragma unroll
+            for (int i = 0; i < 3; i++) Um[3 * i + k] = csub(Um[3 * i + k], cmul(Um[3 * i + q], dot));
+        }
+        double nrm = 0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) nrm += cnorm2(Um[3 * i + k]);
+        nrm = sqrt(nrm);
+        s[k] = fmax(nrm, tiny);
+#pragma unroll
+        for (int i = 0; i < 3; i++) Um[3 * i + k] = cscale(Um[3 * i + k], 1.0 / s[k]);
+    }
+    // the ordering s_0 >= s_1 >= s_2 of the eigenvalues survives up to rounding;
+    // restore it exactly for the phase solve
+    if (s[0] < s[1]) { double t = s[0]; s[0] = s[1]; s[1] = t; swap_cols(Um, Vs, 0, 1); }
+    if (s[1] < s[2]) { double t = s[1]; s[1] = s[2]; s[2] = t; swap_cols(Um, Vs, 1, 2); }
+    if (s[0] < s[1]) { double t = s[0]; s[0] = s[1]; s[1] = t; swap_cols(Um, Vs, 0, 1); }
+    // e^{i phi} = det(U V^dagger)
+    double2 dU = det3(Um), dV = det3(Vs);
+    double2 dd = cmulc(dV, dU);
+    double phi = atan2(dd.y, dd.x);
     double th[3];
     phase_solve(s, phi, th);
     if (parts) {
@@ -215,24 +258,14 @@ BRI_D M3<double2> project_su3(const M3<double2> &A, ProjectionParts *parts = nul
 #pragma unroll
         for (int k = 0; k < 3; k++) { parts->s[k] = s[k]; parts->th[k] = th[k]; }
     }
-    // Y = A V diag(e^{i th}/s) V^dagger
+    // Y = U diag(e^{i th}) V^dagger
     double2 ph[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         double sn, cs;
         sincos(th[k], &sn, &cs);
-        ph[k] = make_double2(cs / s[k], sn / s[k]);
+        ph[k] = make_double2(cs, sn);
     }
-    double2 B[9];  // V diag(ph) V^dagger
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            double2 sum = make_double2(0, 0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) sum = cadd(sum, cmul(cmul(Vs[3 * i + k], ph[k]), cconj(Vs[3 * j + k])));
-            B[3 * i + j] = sum;
-        }
     M3<double2> Y;
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -240,7 +273,7 @@ BRI_D M3<double2> project_su3(const M3<double2> &A, ProjectionParts *parts = nul
         for (int j = 0; j < 3; j++) {
             double2 sum = make_double2(0, 0);
 #pragma unroll
-            for (int k = 0; k < 3; k++) sum = cadd(sum, cmul(A.e[3 * i + k], B[3 * k + j]));
+            for (int k = 0; k < 3; k++) sum = cadd(sum, cmul(cmul(Um[3 * i + k], ph[k]), cconj(Vs[3 * j + k])));
             Y.e[3 * i + j] = sum;
         }
     return Y;

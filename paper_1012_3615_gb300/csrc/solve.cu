@@ -484,8 +484,8 @@ bri_status solve_fp64(bri_ctx *ctx, double2 *x, const double2 *b, double m0, dou
         BRI_RETURN_IF(bicgstab<double2>(ctx, w->v64, b, true, 1, m0, BRI_F64, 0.5 * tol, maxit - total, s, flags, iters));
         total += iters[0];
         BRI_RETURN_IF(true_residual(ctx, (double2 *)w->v64.x, b, w->r64 ? w->r64 : (double2 *)w->v64.t, 1, m0, s, nrm));
+        if (!std::isfinite(nrm[0]) || !std::isfinite(nrm[1])) { st = BRI_ENAN; rel = NAN; break; }
         rel = nrm[1] > 0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
-        if (!std::isfinite(rel)) { st = BRI_ENAN; break; }
         if (rel <= tol) { st = BRI_OK; break; }
         if (flags[0] == 3) { st = BRI_ENAN; break; }
         st = flags[0] == 2 ? BRI_EBREAKDOWN : BRI_ENOTCONV;
@@ -515,8 +515,13 @@ bri_status solve_mixed(bri_ctx *ctx, double2 *x, const double2 *b, int nrhs, dou
         bool all = true;
         for (int r = 0; r < nrhs; r++) {
             if (done[r]) continue;
+            if (!std::isfinite(nrm[2 * r]) || !std::isfinite(nrm[2 * r + 1])) {
+                rel[r] = NAN;
+                done[r] = 1;
+                sts[r] = BRI_ENAN;
+                continue;
+            }
             rel[r] = nrm[2 * r + 1] > 0 ? sqrt(nrm[2 * r] / nrm[2 * r + 1]) : 0.0;
-            if (!std::isfinite(rel[r])) { done[r] = 1; sts[r] = BRI_ENAN; continue; }
             if (rel[r] <= tol) { done[r] = 1; sts[r] = BRI_OK; continue; }
             if (tot[r] >= maxit) { done[r] = 1; sts[r] = BRI_ENOTCONV; continue; }
             all = false;
