@@ -177,10 +177,13 @@ bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, voi
  * Requires the fields of that precision.  Synchronises the stream. */
 bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
 
-/* Set / read the threads per block of the apply kernels for (prec, nrhs)
- * (what bri_tune chooses; 0 < threads <= 1024, rounded down to a multiple of
- * 32 and clamped to the kernel's limit at launch).  bri_get_threads returns
- * the current choice (128 when untuned) or a negative bri_status. */
+/* Set / read the launch shape of the apply kernels for (prec, nrhs) (what
+ * bri_tune chooses): threads per block of the plain kernel (32..1024, rounded
+ * down to a multiple of 32, clamped to the kernel's limit at launch), or 0 for
+ * the shared-memory tiled kernel (FP32 spinors; extents multiples of
+ * 8, 4, 2, 2; otherwise 0 falls back to 128 threads).  bri_get_threads returns
+ * the current choice (untuned: 0 where the tiled kernel applies, else 128) or
+ * a negative bri_status. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "tile.cuh"
 
 using namespace bri;
 
@@ -234,7 +235,8 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream) {
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_prec(ctx, prec));
-    if (nrhs < 1 || threads < 32 || threads > 1024) return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
+    if (nrhs < 1 || threads < 0 || (threads > 0 && threads < 32) || threads > 1024)
+        return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
     ctx->tune[bri_tune_key(ctx, prec, nrhs)] = threads & ~31;
     return BRI_OK;
 }
@@ -265,7 +267,8 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     int best = 128;
     float best_ms = 1e30f;
     bri_status st = BRI_OK;
-    for (int thr : {64, 128, 256, 512}) {
+    for (int thr : {0, 64, 128, 256, 512}) {
+        if (thr == 0 && (prec == BRI_F64 || !tiled_ok(ctx->g))) continue;
         if ((st = bri_dslash_raw(ctx, out, in, nrhs, 0.0, 0, prec, nullptr, thr, s)) != BRI_OK) break;  // warm-up
         cudaEventRecord(e0, s);
         const int reps = 3;

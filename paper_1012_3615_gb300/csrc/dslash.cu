@@ -3,6 +3,7 @@
 
 #include "ctx.h"
 #include "links.cuh"
+#include "tile.cuh"
 
 namespace bri {
 // defined in dslash_kernel.cuh, instantiated once per format in dslash_*.cu
@@ -21,9 +22,12 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
     return buf;
 }
 
+// launch shape: threads per block of the plain kernel, or 0 for the
+// shared-memory tiled kernel (FP32 spinors, extents multiples of the tile)
 int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
     auto it = ctx->tune.find(bri_tune_key(ctx, prec, nrhs));
-    return it == ctx->tune.end() ? 128 : it->second;
+    if (it != ctx->tune.end()) return it->second;
+    return (prec != BRI_F64 && tiled_ok(ctx->g)) ? 0 : 128;
 }
 
 bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,

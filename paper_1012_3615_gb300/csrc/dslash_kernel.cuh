@@ -20,6 +20,7 @@
 
 #include "ctx.h"
 #include "links.cuh"
+#include "tile.cuh"
 
 namespace bri {
 
@@ -77,9 +78,10 @@ template <> struct AccOf<double2> { using A = AccD; };
 
 BRI_D float2 f2(float v) { return make_float2(v, v); }
 
-// FP32 hop with packed FMAs: chi = W psi as sum_c' (psi.re * w + psi.im * (i w))
+// FP32 hop with packed FMAs: chi = W psi as sum_c' (psi.re * w + psi.im * (i w));
+// p is the neighbour spinor, already loaded
 template <int K, int SGN>
-BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, AccF &acc) {
+BRI_D void hop_apply_p(const M3<float2> &W, const float2 p[12], float ph, float rsign, AccF &acc) {
     constexpr int n = off_class(K);
     const float l = (float)lambda_w(n) * ph;
     const float r = (float)rho_w(n) * (ph * rsign);
@@ -92,8 +94,6 @@ BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float 
             A[3 * c + cp] = w;
             B[3 * c + cp] = make_float2(-w.y, w.x);
         }
-    float2 p[12];
-    load_spinor(psi, p);
 #pragma unroll
     for (int sp = 0; sp < 4; sp++) {
         float2 chi[3];
@@ -122,6 +122,13 @@ BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float 
             }
         }
     }
+}
+
+template <int K, int SGN>
+BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, AccF &acc) {
+    float2 p[12];
+    load_spinor(psi, p);
+    hop_apply_p<K, SGN>(W, p, ph, rsign, acc);
 }
 
 // one hop: offset of hypercube index K, reversed when SGN = -1 (then W is the
@@ -237,10 +244,158 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
     store_spinor(out + (size_t)site * 12, o);
 }
 
+// ---- shared-memory tiled variant (FP32 spinors) ------------------------------
+// A CTA owns a TX x TY x TZ x TT tile of sites (one thread per site).  The
+// tile's spinors plus a one-site halo in every direction are copied to shared
+// memory with coalesced 16-byte asynchronous copies (periodic wrap handled on
+// the way in), so each of the 81 neighbour reads is a shared-memory load whose
+// address offset is a compile-time constant.  Sites are padded to 112 bytes (7
+// float4) so a quarter-warp of LDS.128 hits eight distinct bank groups.  The
+// result goes back through shared memory for coalesced stores.
+constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HT = TT + 2;
+constexpr int HSITES = HX * HY * HZ * HT;
+constexpr int SSTR = 7;  // float4 slots per site in shared memory
+constexpr int TILE_THREADS = TX * TY * TZ * TT;
+constexpr int TILE_SMEM = HSITES * SSTR * 16;
+
+BRI_D void lds_spinor(uint32_t addr, float2 o[12]) {
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        float4 v;
+        asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+            : "r"(addr + 16 * i));
+        o[2 * i] = make_float2(v.x, v.y);
+        o[2 * i + 1] = make_float2(v.z, v.w);
+    }
+}
+
+BRI_HD constexpr int halo_delta(int K) {
+    return off_comp(K, 0) + HX * (off_comp(K, 1) + HY * (off_comp(K, 2) + HZ * off_comp(K, 3)));
+}
+
+template <int J, class LL>
+BRI_D void hop_pair_tiled(const LL &ll, uint32_t sbase, int hc, int site, const SiteNb &nb, float rsign, AccF &acc) {
+    constexpr int K = canon_k(J);
+    constexpr int hd = halo_delta(K);
+    {
+        float ph;
+        (void)nb_index<K, 1>(nb, site, ph);
+        M3<float2> W = ll.load(J, site);
+        float2 p[12];
+        lds_spinor(sbase + (uint32_t)((hc + hd) * SSTR * 16), p);
+        hop_apply_p<K, 1>(W, p, ph, rsign, acc);
+    }
+    {
+        float ph;
+        const int y = nb_index<K, -1>(nb, site, ph);
+        M3<float2> W = ll.load(J, y);
+        float2 p[12];
+        lds_spinor(sbase + (uint32_t)((hc - hd) * SSTR * 16), p);
+        hop_apply_p<K, -1>(W, p, ph, rsign, acc);
+    }
+}
+
+template <class LL, int... Js>
+BRI_D void all_hops_tiled(std::integer_sequence<int, Js...>, const LL &ll, uint32_t sbase, int hc, int site,
+                          const SiteNb &nb, float rsign, AccF &acc) {
+    (hop_pair_tiled<Js>(ll, sbase, hc, site, nb, rsign, acc), ...);
+}
+
+template <class LL>
+__global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, const float2 *__restrict__ in,
+                                                               float2 *__restrict__ out, Geom g, double diag,
+                                                               const int *__restrict__ skip) {
+    extern __shared__ float4 smem[];
+    if (skip && skip[blockIdx.y]) return;
+    const size_t off = (size_t)blockIdx.y * g.V * 12;
+    in += off;
+    out += off;
+    // tile origin
+    const int ntx = g.L[0] / TX, nty = g.L[1] / TY, ntz = g.L[2] / TZ;
+    int b = blockIdx.x;
+    const int x0 = (b % ntx) * TX; b /= ntx;
+    const int y0 = (b % nty) * TY; b /= nty;
+    const int z0 = (b % ntz) * TZ; b /= ntz;
+    const int t0 = b * TT;
+    // stage the halo tile: HSITES sites x 6 chunks of 16 bytes
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    for (int c = threadIdx.x; c < HSITES * 6; c += TILE_THREADS) {
+        const int h = c / 6, q = c - 6 * h;
+        int r = h;
+        int gx = x0 - 1 + r % HX; r /= HX;
+        int gy = y0 - 1 + r % HY; r /= HY;
+        int gz = z0 - 1 + r % HZ;
+        int gt = t0 - 1 + r / HZ;
+        gx += gx < 0 ? g.L[0] : (gx >= g.L[0] ? -g.L[0] : 0);
+        gy += gy < 0 ? g.L[1] : (gy >= g.L[1] ? -g.L[1] : 0);
+        gz += gz < 0 ? g.L[2] : (gz >= g.L[2] ? -g.L[2] : 0);
+        gt += gt < 0 ? g.L[3] : (gt >= g.L[3] ? -g.L[3] : 0);
+        const size_t gs = (size_t)gx + (size_t)g.L[0] * (gy + (size_t)g.L[1] * (gz + (size_t)g.L[2] * gt));
+        const float4 *src = reinterpret_cast<const float4 *>(in + gs * 12) + q;
+        const uint32_t dst = sbase + (uint32_t)((h * SSTR + q) * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = (tid / TX) % TY, lz = (tid / (TX * TY)) % TZ, lt = tid / (TX * TY * TZ);
+    const int site = (x0 + lx) + g.L[0] * ((y0 + ly) + g.L[1] * ((z0 + lz) + g.L[2] * (t0 + lt)));
+    const int hc = (lx + 1) + HX * ((ly + 1) + HY * ((lz + 1) + HZ * (lt + 1)));
+    int x[4];
+    const SiteNb nb = site_nb(g, site, x);
+    AccF acc;
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        acc.a[i] = make_float2(0.f, 0.f);
+        acc.ai[i] = make_float2(0.f, 0.f);
+    }
+    const float rsign = mode == 1 ? -1.f : 1.f;
+    all_hops_tiled(std::make_integer_sequence<int, NCANON>{}, ll, sbase, hc, site, nb, rsign, acc);
+    float2 p[12];
+    lds_spinor(sbase + (uint32_t)(hc * SSTR * 16), p);
+    const float dg = (float)diag;
+    float2 o[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        float2 v;
+        v.x = dg * p[i].x + acc.a[i].x - acc.ai[i].y;
+        v.y = dg * p[i].y + acc.a[i].y + acc.ai[i].x;
+        if (mode == 2 && i >= 6) { v.x = -v.x; v.y = -v.y; }
+        o[i] = v;
+    }
+    // write the tile through shared memory (tile-local order, 7 slots per site)
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+        smem[tid * SSTR + i] = make_float4(o[2 * i].x, o[2 * i].y, o[2 * i + 1].x, o[2 * i + 1].y);
+    __syncthreads();
+    for (int c = threadIdx.x; c < TILE_THREADS * 6; c += TILE_THREADS) {
+        const int h = c / 6, q = c - 6 * h;
+        const int hx = h % TX, hy = (h / TX) % TY, hz = (h / (TX * TY)) % TZ, ht = h / (TX * TY * TZ);
+        const size_t gs = (size_t)(x0 + hx) + (size_t)g.L[0] * ((y0 + hy) + (size_t)g.L[1] * ((z0 + hz) + (size_t)g.L[2] * (t0 + ht)));
+        reinterpret_cast<float4 *>(out + gs * 12)[q] = smem[h * SSTR + q];
+    }
+}
+
 template <class LL>
 void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
                    const int *skip, int threads, cudaStream_t s) {
     using T = typename LL::T;
+    if constexpr (sizeof(T) == 8) {
+        if (threads == 0 && tiled_ok(g)) {
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_dslash_tiled<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+                attr_set = true;
+            }
+            dim3 grid((unsigned)(g.V / TILE_THREADS), (unsigned)nrhs);
+            k_dslash_tiled<<<grid, TILE_THREADS, TILE_SMEM, s>>>(mode, ll, (const float2 *)in, (float2 *)out, g,
+                                                                   diag, skip);
+            return;
+        }
+    }
+    if (threads == 0) threads = 128;
     static int max_threads = 0;  // per-kernel limit from its register use
     if (max_threads == 0) {
         cudaFuncAttributes attr;

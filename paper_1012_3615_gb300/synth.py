@@ -122,10 +122,34 @@ def plane_wave(L, k, u):
     return np.ascontiguousarray(ph[:, None, None] * np.asarray(u, np.complex128)[None])
 
 
+def _det3_torch(M):
+    return (M[:, 0, 0] * (M[:, 1, 1] * M[:, 2, 2] - M[:, 1, 2] * M[:, 2, 1])
+            - M[:, 0, 1] * (M[:, 1, 0] * M[:, 2, 2] - M[:, 1, 2] * M[:, 2, 0])
+            + M[:, 0, 2] * (M[:, 1, 0] * M[:, 2, 1] - M[:, 1, 1] * M[:, 2, 0]))
+
+
+def _expm_i_torch(X):
+    """exp(X) for a batch of small anti-hermitian 3x3 matrices by Taylor series
+    with scaling and squaring (matmuls only)."""
+    import torch
+
+    k = 6  # ||X|| / 64 is far below 1 for these inputs
+    Y = X / (2 ** k)
+    eye = torch.eye(3, dtype=X.dtype, device=X.device).expand_as(Y)
+    E = eye.clone()
+    term = eye.clone()
+    for n in range(1, 13):
+        term = term @ Y / n
+        E = E + term
+    for _ in range(k):
+        E = E @ E
+    return E
+
+
 def random_su3_links_torch(L, eps, seed, device="cuda", chunk=1 << 20):
     """Same distribution as random_su3_links, drawn with torch on the device
     (for lattices too large to generate on the host in reasonable time; the
-    random stream differs from the numpy one)."""
+    random stream differs from the numpy one).  Uses matmuls only."""
     import torch
 
     V = volume(L)
@@ -137,8 +161,9 @@ def random_su3_links_torch(L, eps, seed, device="cuda", chunk=1 << 20):
         e = min(V * 4, s + chunk)
         h = torch.randn((e - s, 8), generator=g, dtype=torch.float64, device=device)
         H = torch.einsum("na,aij->nij", h.to(torch.complex128), lam) / 2.0
-        M = torch.linalg.matrix_exp(1j * eps * H)
-        det = torch.linalg.det(M)
+        M = _expm_i_torch(1j * eps * H)
+        M = M @ (1.5 * torch.eye(3, dtype=M.dtype, device=device) - 0.5 * M.conj().transpose(1, 2) @ M)
+        det = _det3_torch(M)
         U[s:e] = M / (det ** (1.0 / 3.0))[:, None, None]
     return U.reshape(V, 4, 3, 3)
 

@@ -13,6 +13,9 @@ AP = (1, 1, 1, -1)
 PER = (1, 1, 1, 1)
 
 CASES = [((4, 4, 4, 4), AP), ((3, 5, 4, 6), AP), ((4, 3, 3, 4), PER), ((3, 3, 3, 3), AP)]
+# extents that are multiples of the shared-memory tile (8, 4, 2, 2): FP32 applies
+# there use the tiled kernel by default
+TILED = [((8, 4, 4, 4), AP), ((16, 8, 6, 4), PER)]
 
 
 def _setup(L, bc, seed, nrhs=2, eps=0.4):
@@ -47,7 +50,7 @@ def test_fp64_apply_dagger_overlap(gpu, L, bc):
 
 
 @pytest.mark.parametrize("comp,tol", [("full", 1e-6), ("2row", 1e-6), ("8param", 2e-5)])
-@pytest.mark.parametrize("L,bc", CASES[:2])
+@pytest.mark.parametrize("L,bc", CASES[:2] + TILED)
 def test_fp32_apply(gpu, L, bc, comp, tol):
     U, psi, W = _setup(L, bc, 10 + sum(L))
     op = Brillouin(L, bc)
@@ -72,6 +75,24 @@ def test_fp16_links_apply(gpu, comp, tol):
     out = op.apply(x, m0=0.0, prec="f16").cpu().numpy()
     for r in range(psi.shape[0]):
         assert _rel_l2(out[r], oracle.apply(L, bc, W, 0.0, psi[r])) < tol
+
+
+@pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f32", "2row"), ("f16", "2row")])
+def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
+    """The shared-memory tiled kernel performs the same arithmetic in the same
+    order as the plain one: results are bitwise equal, for every mode."""
+    L, bc = (16, 8, 6, 4), AP
+    U = synth.random_su3_links(L, 0.4, 31)
+    psi = synth.gaussian_spinor(L, 3, 32).astype(np.complex64)
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+    x = torch.as_tensor(psi, device=gpu)
+    assert op.threads(prec, 3) == 0  # tiled by default here
+    tiled = [op.apply(x, 0.1, prec=prec), op.apply(x, 0.1, dagger=True, prec=prec), op.overlap_kernel(x, 1.0, prec=prec)]
+    op.set_threads(prec, 3, 128)
+    plain = [op.apply(x, 0.1, prec=prec), op.apply(x, 0.1, dagger=True, prec=prec), op.overlap_kernel(x, 1.0, prec=prec)]
+    for a, b in zip(tiled, plain):
+        assert torch.equal(a, b)
 
 
 def test_multi_rhs_equals_single(gpu):
