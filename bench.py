@@ -240,7 +240,7 @@ def native(args, world, rank, local, pg):
     sdt = torch.complex128 if prec == "f64" else torch.complex64
     x = synth.gaussian_spinor_torch(L, nrhs, SEED + 100 + rank, device=dev, dtype=sdt)
     out = torch.empty_like(x)
-    if args.threads:
+    if args.threads is not None:
         op.set_threads(prec, nrhs, args.threads)
     else:
         op.tune(prec, nrhs)
@@ -346,7 +346,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lattice", type=lambda t: [int(v) for v in t.split(",")], default=None,
                     help="lattice extents x,y,z,t (default 32,32,32,64)")
-    ap.add_argument("--threads", type=int, default=0, help="fixed threads per block (skips the tuner)")
+    ap.add_argument("--threads", type=int, default=None,
+                    help="fixed launch shape (threads per block; 0 = shared-memory tiled kernel); skips the tuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local, pg = dist_setup(args)

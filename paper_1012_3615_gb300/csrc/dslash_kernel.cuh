@@ -124,6 +124,79 @@ BRI_D void hop_apply_p(const M3<float2> &W, const float2 p[12], float ph, float 
     }
 }
 
+// Same arithmetic as hop_apply_p with the offset d a runtime value: the FP32
+// kernels loop over the 40 (d, -d) pairs instead of unrolling them, which keeps
+// the kernel small enough for the instruction cache (the unrolled form stalls
+// on instruction fetch).  The gamma terms are taken under warp-uniform branches
+// on d_mu, so no arithmetic is wasted; the spin permutations stay compile-time.
+template <int SGN>
+BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, const int dm[4], AccF &acc) {
+    float2 A[9], B[9];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) {
+            const float2 w = SGN > 0 ? W.e[3 * c + cp] : make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
+            A[3 * c + cp] = w;
+            B[3 * c + cp] = make_float2(-w.y, w.x);
+        }
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        float2 chi[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
+            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
+            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
+            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
+            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
+            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
+            chi[c] = t;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc.a[3 * sp + c] = __ffma2_rn(f2(l), chi[c], acc.a[3 * sp + c]);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (dm[mu] == 0) continue;  // uniform across the warp
+            const int s = gcol(mu, sp);
+            const int gr = gre(mu, s), gi = gim(mu, s);
+            const float cf = r * (float)(SGN * dm[mu] * (gr != 0 ? gr : gi));
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.a[3 * s + c]);
+                else acc.ai[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.ai[3 * s + c]);
+            }
+        }
+    }
+}
+
+// offset, class weights and neighbour (index, phase) of canonical field j
+struct HopGeo {
+    int dm[4];
+    float lam, rho;
+    int yf, yb;
+    float phf, phb;
+};
+BRI_D HopGeo hop_geo(int j, int site, const SiteNb &nb, float rsign) {
+    HopGeo h;
+    const int k = j + 41;
+    h.dm[0] = k % 3 - 1;
+    h.dm[1] = (k / 3) % 3 - 1;
+    h.dm[2] = (k / 9) % 3 - 1;
+    h.dm[3] = k / 27 - 1;
+    const int n = abs(h.dm[0]) + abs(h.dm[1]) + abs(h.dm[2]) + abs(h.dm[3]);
+    h.lam = -(float)(1 << (4 - n)) * (1.f / 128.f);          // lambda_n, n >= 1
+    h.rho = (float)(1 << (8 - 2 * n)) * (1.f / 432.f) * rsign;  // rho_n
+    h.yf = h.yb = site;
+    h.phf = h.phb = 1.f;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (h.dm[mu] > 0) { h.yf += nb.fw[mu]; h.phf *= nb.sfw[mu]; h.yb += nb.bw[mu]; h.phb *= nb.sbw[mu]; }
+        if (h.dm[mu] < 0) { h.yf += nb.bw[mu]; h.phf *= nb.sbw[mu]; h.yb += nb.fw[mu]; h.phb *= nb.sfw[mu]; }
+    }
+    return h;
+}
+
 template <int K, int SGN>
 BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, AccF &acc) {
     float2 p[12];
@@ -224,7 +297,26 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
         for (int i = 0; i < 12; i++) acc.ai[i] = mk<T>(0, 0);
     }
     const float rsign = mode == 1 ? -1.f : 1.f;
-    all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll 1
+        for (int j = 0; j < NCANON; j++) {
+            const HopGeo h = hop_geo(j, site, nb, rsign);
+            {
+                M3<float2> W = ll.load(j, site);
+                float2 q[12];
+                load_spinor(in + (size_t)h.yf * 12, q);
+                hop_body<1>(W, q, h.lam * h.phf, h.rho * h.phf, h.dm, acc);
+            }
+            {
+                M3<float2> W = ll.load(j, h.yb);
+                float2 q[12];
+                load_spinor(in + (size_t)h.yb * 12, q);
+                hop_body<-1>(W, q, h.lam * h.phb, h.rho * h.phb, h.dm, acc);
+            }
+        }
+    } else {
+        all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
+    }
     T p[12];
     load_spinor(in + (size_t)site * 12, p);
     const R dg = (R)diag;
@@ -272,34 +364,6 @@ BRI_D void lds_spinor(uint32_t addr, float2 o[12]) {
 
 BRI_HD constexpr int halo_delta(int K) {
     return off_comp(K, 0) + HX * (off_comp(K, 1) + HY * (off_comp(K, 2) + HZ * off_comp(K, 3)));
-}
-
-template <int J, class LL>
-BRI_D void hop_pair_tiled(const LL &ll, uint32_t sbase, int hc, int site, const SiteNb &nb, float rsign, AccF &acc) {
-    constexpr int K = canon_k(J);
-    constexpr int hd = halo_delta(K);
-    {
-        float ph;
-        (void)nb_index<K, 1>(nb, site, ph);
-        M3<float2> W = ll.load(J, site);
-        float2 p[12];
-        lds_spinor(sbase + (uint32_t)((hc + hd) * SSTR * 16), p);
-        hop_apply_p<K, 1>(W, p, ph, rsign, acc);
-    }
-    {
-        float ph;
-        const int y = nb_index<K, -1>(nb, site, ph);
-        M3<float2> W = ll.load(J, y);
-        float2 p[12];
-        lds_spinor(sbase + (uint32_t)((hc - hd) * SSTR * 16), p);
-        hop_apply_p<K, -1>(W, p, ph, rsign, acc);
-    }
-}
-
-template <class LL, int... Js>
-BRI_D void all_hops_tiled(std::integer_sequence<int, Js...>, const LL &ll, uint32_t sbase, int hc, int site,
-                          const SiteNb &nb, float rsign, AccF &acc) {
-    (hop_pair_tiled<Js>(ll, sbase, hc, site, nb, rsign, acc), ...);
 }
 
 template <class LL>
@@ -351,7 +415,23 @@ __global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, 
         acc.ai[i] = make_float2(0.f, 0.f);
     }
     const float rsign = mode == 1 ? -1.f : 1.f;
-    all_hops_tiled(std::make_integer_sequence<int, NCANON>{}, ll, sbase, hc, site, nb, rsign, acc);
+#pragma unroll 1
+    for (int j = 0; j < NCANON; j++) {
+        const HopGeo h = hop_geo(j, site, nb, rsign);
+        const int hd = h.dm[0] + HX * (h.dm[1] + HY * (h.dm[2] + HZ * h.dm[3]));
+        {
+            M3<float2> W = ll.load(j, site);
+            float2 q[12];
+            lds_spinor(sbase + (uint32_t)((hc + hd) * SSTR * 16), q);
+            hop_body<1>(W, q, h.lam * h.phf, h.rho * h.phf, h.dm, acc);
+        }
+        {
+            M3<float2> W = ll.load(j, h.yb);
+            float2 q[12];
+            lds_spinor(sbase + (uint32_t)((hc - hd) * SSTR * 16), q);
+            hop_body<-1>(W, q, h.lam * h.phb, h.rho * h.phb, h.dm, acc);
+        }
+    }
     float2 p[12];
     lds_spinor(sbase + (uint32_t)(hc * SSTR * 16), p);
     const float dg = (float)diag;
