@@ -171,6 +171,24 @@ bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double
  * A, Y: device, [n][3][3] complex128 (may alias).  Errors: BRI_EINVAL. */
 bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, void *stream);
 
+/* Hop precompute that allocates nothing, for callers that cannot allocate
+ * device memory (an application whose own pool owns all device memory, an
+ * embedding that must not grow its device footprint while running).  The
+ * paper has no counterpart: it is the computation of bri_build_hops (path
+ * sums of Sec. 5.1 and FP64 back-projection of Sec. 5.2) as a stateless call.
+ *   lat: the lattice, at most 4096 sites;  U: device, [V][4][3][3] complex128;
+ *   W:   device output, [V][40][3][3] complex128, the layout of bri_get_hops.
+ * The path sums live in a fixed scratch array inside the library (81 x 144
+ * bytes per site for 4096 sites, about 45.6 MiB, held on every GPU that loads
+ * the library until the process exits).  All calls share it and it keeps the
+ * last call's contents (nothing needs to start at zero); calls that overlap
+ * on the GPU race, so the caller serialises them.  The first call on a device
+ * looks up the array's device address with that device current: make it
+ * before any stream capture.  Errors (message via bri_last_error(NULL)):
+ * BRI_EINVAL (null or misaligned pointers, extents < 3, bad bc_sign, more
+ * than 4096 sites), BRI_ECUDA. */
+bri_status bri_build_hops_noalloc(const bri_lattice *lat, const double *U, double *W, void *stream);
+
 /* Tune the launch shape of the apply kernels for (prec, nrhs) on this
  * lattice (timed with CUDA events, result cached in the context and, when the
  * environment variable BRI_TUNE_CACHE names a file, in that file).

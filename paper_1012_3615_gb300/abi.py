@@ -47,6 +47,7 @@ SIGNATURES = {
     "bri_force_inverse": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                   ctypes.POINTER(bri_solve_info), c_void_p]),
     "bri_project_su3": (c_int, [c_void_p, c_void_p, c_void_p, c_long, c_void_p]),
+    "bri_build_hops_noalloc": (c_int, [ctypes.POINTER(bri_lattice), c_void_p, c_void_p, c_void_p]),
     "bri_tune": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "bri_set_threads": (c_int, [c_void_p, c_int, c_int, c_int]),
     "bri_get_threads": (c_int, [c_void_p, c_int, c_int]),

@@ -143,3 +143,20 @@ class Brillouin:
 
     def kernel_launches(self):
         return int(self.lib.bri_kernel_launches(self.ctx))
+
+
+def build_hops_noalloc(L, bc, U, out=None):
+    """The 40 canonical hopping fields of links U (cuda complex128 (V, 4, 3, 3))
+    computed without any device allocation by the library (at most 4096
+    sites); returns (V, 40, 3, 3) complex128 in out (allocated here if None)."""
+    lib = abi.load()
+    L = tuple(int(v) for v in L)
+    V = L[0] * L[1] * L[2] * L[3]
+    if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous() and U.numel() == V * 36):
+        raise ValueError("U must be a contiguous cuda complex128 (V, 4, 3, 3) tensor")
+    out = torch.empty((V, 40, 3, 3), dtype=torch.complex128, device=U.device) if out is None else out
+    lat = abi.bri_lattice((ctypes.c_int * 4)(*L), (ctypes.c_int * 4)(*[int(v) for v in bc]))
+    st = lib.bri_build_hops_noalloc(ctypes.byref(lat), _ptr(U), _ptr(out), _stream())
+    if st != 0:
+        raise BriError(st, lib.bri_last_error(None).decode())
+    return out

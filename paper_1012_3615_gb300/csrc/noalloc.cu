@@ -21,8 +21,7 @@
 #include <cstring>
 #include <string>
 
-#include "brillouin.h"
-#include "common.cuh"
+#include "ctx.h"
 #include "project.cuh"
 
 using namespace bri;
@@ -35,7 +34,6 @@ static __device__ __align__(256) unsigned char
 
 namespace {
 
-std::string g_noalloc_error;
 void *g_scratch_addr[BRI_NOALLOC_MAX_DEVICES];
 bool g_scratch_ready[BRI_NOALLOC_MAX_DEVICES];
 
@@ -84,14 +82,10 @@ __global__ void k_na_project(const M3<double2> *__restrict__ A, double2 *__restr
     for (int e = 0; e < 9; e++) W[((size_t)site * NCANON + j) * 9 + e] = w.e[e];
 }
 
-bri_status fail(bri_status st, const char *msg) {
-    g_noalloc_error = msg;
-    return st;
-}
+// errors of this stateless entry point are reported through bri_last_error(NULL)
+bri_status fail(bri_status st, const std::string &msg) { return bri_fail(nullptr, st, msg); }
 
 }  // namespace
-
-const char *bri_noalloc_last_error() { return g_noalloc_error.c_str(); }
 
 extern "C" bri_status bri_build_hops_noalloc(const bri_lattice *lat, const double *U, double *W, void *stream) {
     if (!lat || !U || !W) return fail(BRI_EINVAL, "bri_build_hops_noalloc: null argument");
@@ -116,10 +110,8 @@ extern "C" bri_status bri_build_hops_noalloc(const bri_lattice *lat, const doubl
     if (!g_scratch_ready[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_hop_scratch);
-        if (e != cudaSuccess || !p) {
-            g_noalloc_error = std::string("bri_build_hops_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return BRI_ECUDA;
-        }
+        if (e != cudaSuccess || !p)
+            return fail(BRI_ECUDA, std::string("bri_build_hops_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
         g_scratch_ready[dev] = true;
     }
