@@ -328,8 +328,77 @@ def native(args, world, rank, local, pg):
                                              "TFLOP/s": FLOPS_PER_SITE * nr * V / (t * 1e-3) / 1e12}
                 del xx, oo
         line["sweep"] = sweep
+    if args.solve:
+        del op, x, out
+        torch.cuda.empty_cache()
+        line["solve"] = solve_bench(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def solve_bench(args, dev):
+    """Solver workloads: time to a true FP64 residual of 1e-10.
+    A: 16^3x32, m0 = -0.05, links exp(i0.4H), Z2 source, hops FP32 2-row / FP16 2-row:
+       FP64 BiCGstab vs mixed defect correction (FP32 and FP16 inner).
+    B: 24^3x48, m0 = 0, links exp(i0.35H), 12 spin-colour point sources at one site,
+       FP16 2-row hops: one batched solve of all 12 vs 12 sequential mixed (FP16) solves,
+       and the FP64 time of the first source."""
+    import numpy as np
+    import torch
+
+    from paper_1012_3615_gb300 import Brillouin, synth
+
+    out = {}
+    L = (16, 16, 16, 32)
+    U = synth.random_su3_links_torch(L, 0.4, SEED + 2, device=dev)
+    op = Brillouin(L, BC)
+    op.build_hops(U, prec="f32", comp="2row")
+    op.store_hops("f16", "2row")
+    b = torch.as_tensor(synth.z2_spinor(L, 1, SEED + 3), device=dev)
+    res = {}
+    for mode, name in ((0, "fp64"), (1, "mixed_f32"), (2, "mixed_f16")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = op.solve(b, m0=-0.05, tol=1e-10, maxit=20000, mode=mode)
+        torch.cuda.synchronize()
+        res[name] = dict(info[0], seconds=time.perf_counter() - t0)
+    res["speedup_mixed_f32_vs_fp64"] = res["fp64"]["seconds"] / res["mixed_f32"]["seconds"]
+    res["speedup_mixed_f16_vs_fp64"] = res["fp64"]["seconds"] / res["mixed_f16"]["seconds"]
+    out["solve_16x16x16x32"] = res
+    del op, U
+    if not args.solve_small:
+        L = (24, 24, 24, 48)
+        V = synth.volume(L)
+        U = synth.random_su3_links_torch(L, 0.35, SEED + 4, device=dev)
+        op = Brillouin(L, BC)
+        op.build_hops(U, prec="f16", comp="2row")
+        x0 = int(np.random.default_rng(SEED + 5).integers(0, V))
+        b = torch.zeros((12, V, 4, 3), dtype=torch.complex128, device=dev)
+        for s_ in range(4):
+            for c in range(3):
+                b[3 * s_ + c, x0, s_, c] = 1.0
+        res = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=3)
+        torch.cuda.synchronize()
+        res["batched_12"] = {"seconds": time.perf_counter() - t0, "iters": [i["iters"] for i in info],
+                             "outer": [i["outer_iters"] for i in info],
+                             "true_resid_max": max(i["true_resid"] for i in info),
+                             "status": sorted(set(i["status"] for i in info))}
+        t0 = time.perf_counter()
+        xs, infs = op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=2)  # one after the other
+        torch.cuda.synchronize()
+        res["sequential_12_mixed_f16"] = {"seconds": time.perf_counter() - t0,
+                                          "true_resid_max": max(i["true_resid"] for i in infs)}
+        t0 = time.perf_counter()
+        x1, inf1 = op.solve(b[:1].contiguous(), m0=0.0, tol=1e-10, maxit=20000, mode=0)
+        torch.cuda.synchronize()
+        res["fp64_first_source"] = dict(inf1[0], seconds=time.perf_counter() - t0)
+        res["speedup_batched_vs_sequential_mixed"] = res["sequential_12_mixed_f16"]["seconds"] / res["batched_12"]["seconds"]
+        res["speedup_batched_vs_12x_fp64"] = 12 * res["fp64_first_source"]["seconds"] / res["batched_12"]["seconds"]
+        out["solve_24x24x24x48_12_point_sources"] = res
+    return out
 
 
 def main():
@@ -341,7 +410,8 @@ def main():
     ap.add_argument("--mode", default="f32-full", choices=sorted(LINK_BYTES))
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--sweep", action="store_true")
-    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--solve", action="store_true", help="add the solver workloads (time to 1e-10)")
+    ap.add_argument("--solve-small", action="store_true", help="only the 16^3x32 solver workload")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lattice", type=lambda t: [int(v) for v in t.split(",")], default=None,

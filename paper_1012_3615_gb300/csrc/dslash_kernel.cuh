@@ -170,31 +170,95 @@ BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, c
     }
 }
 
-// offset, class weights and neighbour (index, phase) of canonical field j
-struct HopGeo {
+
+// Per-field constants of the 40 canonical offsets (offset, class weights and
+// the offset within the shared-memory halo tile), read from the constant cache
+// with a warp-uniform index.
+struct HopConst {
     int dm[4];
     float lam, rho;
-    int yf, yb;
-    float phf, phb;
+    int hd;
 };
-BRI_D HopGeo hop_geo(int j, int site, const SiteNb &nb, float rsign) {
-    HopGeo h;
-    const int k = j + 41;
-    h.dm[0] = k % 3 - 1;
-    h.dm[1] = (k / 3) % 3 - 1;
-    h.dm[2] = (k / 9) % 3 - 1;
-    h.dm[3] = k / 27 - 1;
-    const int n = abs(h.dm[0]) + abs(h.dm[1]) + abs(h.dm[2]) + abs(h.dm[3]);
-    h.lam = -(float)(1 << (4 - n)) * (1.f / 128.f);          // lambda_n, n >= 1
-    h.rho = (float)(1 << (8 - 2 * n)) * (1.f / 432.f) * rsign;  // rho_n
-    h.yf = h.yb = site;
-    h.phf = h.phb = 1.f;
+BRI_HD constexpr HopConst make_hop(int j) {
+    const int k = canon_k(j);
+    const int n = off_class(k);
+    return HopConst{{off_comp(k, 0), off_comp(k, 1), off_comp(k, 2), off_comp(k, 3)},
+                    (float)lambda_w(n),
+                    (float)rho_w(n),
+                    off_comp(k, 0) + (TX + 2) * (off_comp(k, 1) + (TY + 2) * (off_comp(k, 2) + (TZ + 2) * off_comp(k, 3)))};
+}
+#define BRI_H4(j) make_hop(j), make_hop(j + 1), make_hop(j + 2), make_hop(j + 3)
+static __constant__ HopConst c_hop[NCANON] = {BRI_H4(0),  BRI_H4(4),  BRI_H4(8),  BRI_H4(12), BRI_H4(16),
+                                              BRI_H4(20), BRI_H4(24), BRI_H4(28), BRI_H4(32), BRI_H4(36)};
+#undef BRI_H4
+
+// neighbour index and boundary phase of the forward (d) and reversed (-d) hop
+BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &phf, int &yb, float &phb) {
+    yf = yb = site;
+    phf = phb = 1.f;
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-        if (h.dm[mu] > 0) { h.yf += nb.fw[mu]; h.phf *= nb.sfw[mu]; h.yb += nb.bw[mu]; h.phb *= nb.sbw[mu]; }
-        if (h.dm[mu] < 0) { h.yf += nb.bw[mu]; h.phf *= nb.sbw[mu]; h.yb += nb.fw[mu]; h.phb *= nb.sfw[mu]; }
+        if (dm[mu] > 0) { yf += nb.fw[mu]; phf *= nb.sfw[mu]; yb += nb.bw[mu]; phb *= nb.sbw[mu]; }
+        else if (dm[mu] < 0) { yf += nb.bw[mu]; phf *= nb.sbw[mu]; yb += nb.fw[mu]; phb *= nb.sfw[mu]; }
     }
-    return h;
+}
+
+// FP32 stencil over the 40 (d, -d) pairs as a compact loop.  PF = true loads
+// the two links of pair j + 1 while pair j is computed (links stream from
+// DRAM; the neighbour spinors mostly hit L1/L2).
+template <bool PF, class LL>
+BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
+                    AccF &acc) {
+    if constexpr (!PF) {
+#pragma unroll 1
+        for (int j = 0; j < NCANON; j++) {
+            const HopConst hc = c_hop[j];
+            int yf, yb;
+            float phf, phb;
+            hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+            {
+                M3<float2> W = ll.load(j, site);
+                float2 q[12];
+                load_spinor(in + (size_t)yf * 12, q);
+                hop_body<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
+            }
+            {
+                M3<float2> W = ll.load(j, yb);
+                float2 q[12];
+                load_spinor(in + (size_t)yb * 12, q);
+                hop_body<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
+            }
+        }
+    } else {
+        HopConst hc = c_hop[0];
+        int yf, yb;
+        float phf, phb;
+        hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+        M3<float2> Wf = ll.load(0, site), Wb = ll.load(0, yb);
+#pragma unroll 2
+        for (int j = 0; j < NCANON; j++) {
+            const HopConst h = hc;
+            const int cyf = yf, cyb = yb;
+            const float cphf = phf, cphb = phb;
+            const M3<float2> Wf0 = Wf, Wb0 = Wb;
+            if (j + 1 < NCANON) {
+                hc = c_hop[j + 1];
+                hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+                Wf = ll.load(j + 1, site);
+                Wb = ll.load(j + 1, yb);
+            }
+            {
+                float2 q[12];
+                load_spinor(in + (size_t)cyf * 12, q);
+                hop_body<1>(Wf0, q, h.lam * cphf, h.rho * rsign * cphf, h.dm, acc);
+            }
+            {
+                float2 q[12];
+                load_spinor(in + (size_t)cyb * 12, q);
+                hop_body<-1>(Wb0, q, h.lam * cphb, h.rho * rsign * cphb, h.dm, acc);
+            }
+        }
+    }
 }
 
 template <int K, int SGN>
@@ -276,7 +340,7 @@ BRI_D void all_hops(std::integer_sequence<int, Js...>, const LL &ll, const typen
     (hop_pair<Js>(ll, in, site, nb, rsign, acc), ...);
 }
 
-template <class LL>
+template <class LL, bool PF>
 __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out, Geom g,
                          double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
@@ -298,22 +362,7 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
     }
     const float rsign = mode == 1 ? -1.f : 1.f;
     if constexpr (sizeof(T) == 8) {
-#pragma unroll 1
-        for (int j = 0; j < NCANON; j++) {
-            const HopGeo h = hop_geo(j, site, nb, rsign);
-            {
-                M3<float2> W = ll.load(j, site);
-                float2 q[12];
-                load_spinor(in + (size_t)h.yf * 12, q);
-                hop_body<1>(W, q, h.lam * h.phf, h.rho * h.phf, h.dm, acc);
-            }
-            {
-                M3<float2> W = ll.load(j, h.yb);
-                float2 q[12];
-                load_spinor(in + (size_t)h.yb * 12, q);
-                hop_body<-1>(W, q, h.lam * h.phb, h.rho * h.phb, h.dm, acc);
-            }
-        }
+        f32_hops<PF>(ll, in, site, nb, rsign, acc);
     } else {
         all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
     }
@@ -417,19 +466,21 @@ __global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, 
     const float rsign = mode == 1 ? -1.f : 1.f;
 #pragma unroll 1
     for (int j = 0; j < NCANON; j++) {
-        const HopGeo h = hop_geo(j, site, nb, rsign);
-        const int hd = h.dm[0] + HX * (h.dm[1] + HY * (h.dm[2] + HZ * h.dm[3]));
+        const HopConst h = c_hop[j];
+        int yf, yb;
+        float phf, phb;
+        hop_nb(h.dm, site, nb, yf, phf, yb, phb);
         {
             M3<float2> W = ll.load(j, site);
             float2 q[12];
-            lds_spinor(sbase + (uint32_t)((hc + hd) * SSTR * 16), q);
-            hop_body<1>(W, q, h.lam * h.phf, h.rho * h.phf, h.dm, acc);
+            lds_spinor(sbase + (uint32_t)((hc + h.hd) * SSTR * 16), q);
+            hop_body<1>(W, q, h.lam * phf, h.rho * rsign * phf, h.dm, acc);
         }
         {
-            M3<float2> W = ll.load(j, h.yb);
+            M3<float2> W = ll.load(j, yb);
             float2 q[12];
-            lds_spinor(sbase + (uint32_t)((hc - hd) * SSTR * 16), q);
-            hop_body<-1>(W, q, h.lam * h.phb, h.rho * h.phb, h.dm, acc);
+            lds_spinor(sbase + (uint32_t)((hc - h.hd) * SSTR * 16), q);
+            hop_body<-1>(W, q, h.lam * phb, h.rho * rsign * phb, h.dm, acc);
         }
     }
     float2 p[12];
@@ -463,7 +514,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
                    const int *skip, int threads, cudaStream_t s) {
     using T = typename LL::T;
     if constexpr (sizeof(T) == 8) {
-        if (threads == 0 && tiled_ok(g)) {
+        if ((threads & 2047) == 0 && (threads >> 11) == 0 && tiled_ok(g)) {
             static bool attr_set = false;
             if (!attr_set) {
                 cudaFuncSetAttribute(k_dslash_tiled<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
@@ -475,15 +526,35 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
             return;
         }
     }
+    // launch shape: threads per block in the low 11 bits, kernel variant above
+    const int variant = threads >> 11;
+    threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads = 0;  // per-kernel limit from its register use
-    if (max_threads == 0) {
-        cudaFuncAttributes attr;
-        max_threads = cudaFuncGetAttributes(&attr, k_dslash<LL>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+    static int max_threads[2] = {0, 0};  // per-kernel limit from its register use
+    dim3 grid;
+    if constexpr (sizeof(T) == 8) {
+        const int v = variant == 1 ? 1 : 0;
+        if (max_threads[v] == 0) {
+            cudaFuncAttributes attr;
+            cudaError_t e = v ? cudaFuncGetAttributes(&attr, k_dslash<LL, true>)
+                              : cudaFuncGetAttributes(&attr, k_dslash<LL, false>);
+            max_threads[v] = e == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+        }
+        if (threads > max_threads[v]) threads = max_threads[v] & ~31;
+        grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
+        if (v) k_dslash<LL, true><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else k_dslash<LL, false><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+    } else {
+        (void)variant;
+        if (max_threads[0] == 0) {
+            cudaFuncAttributes attr;
+            max_threads[0] =
+                cudaFuncGetAttributes(&attr, k_dslash<LL, false>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+        }
+        if (threads > max_threads[0]) threads = max_threads[0] & ~31;
+        grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
+        k_dslash<LL, false><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
     }
-    if (threads > max_threads) threads = max_threads & ~31;
-    dim3 grid((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
-    k_dslash<<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
 }
 
 }  // namespace bri
