@@ -200,7 +200,9 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * down to a multiple of 32, clamped to the kernel's limit at launch), or 0 for
  * the shared-memory tiled kernel (FP32 spinors; extents multiples of
  * 8, 4, 2, 2; otherwise 0 falls back to 128 threads).  Adding 2048 selects
- * the link-prefetching variant of the plain FP32 kernel.  bri_get_threads returns
+ * the register link-prefetch variant of the plain FP32 kernel, adding 4096
+ * the cp.async shared-memory link-prefetch variant (at most 256 threads).
+ * bri_get_threads returns
  * the current choice (untuned: 0 where the tiled kernel applies, else 128) or
  * a negative bri_status. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);

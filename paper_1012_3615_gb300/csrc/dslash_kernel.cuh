@@ -261,6 +261,51 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
     }
 }
 
+// FP32 stencil loop with the links of pair j + 1 copied asynchronously
+// (cp.async) into this thread's double-buffered shared-memory slots while pair
+// j is computed: the DRAM latency of the links overlaps the arithmetic and
+// costs no registers.  lbase: this thread's slots (2 stages x 2 links).
+template <class LL>
+BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
+                            uint32_t lbase, AccF &acc) {
+    constexpr uint32_t LB = LL::SLOTS * 16;  // bytes per field
+    HopConst hc = c_hop[0];
+    int yf, yb;
+    float phf, phb;
+    hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+    ll.prefetch(0, site, lbase);
+    ll.prefetch(0, yb, lbase + LB);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+#pragma unroll 1
+    for (int j = 0; j < NCANON; j++) {
+        const HopConst h = hc;
+        const int cyf = yf, cyb = yb;
+        const float cphf = phf, cphb = phb;
+        const uint32_t cur = lbase + (uint32_t)(j & 1) * 2 * LB;
+        if (j + 1 < NCANON) {
+            hc = c_hop[j + 1];
+            hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+            const uint32_t nxt = lbase + (uint32_t)((j + 1) & 1) * 2 * LB;
+            ll.prefetch(j + 1, site, nxt);
+            ll.prefetch(j + 1, yb, nxt + LB);
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;" ::: "memory");
+        {
+            const M3<float2> W = ll.load_smem(cur);
+            float2 q[12];
+            load_spinor(in + (size_t)cyf * 12, q);
+            hop_body<1>(W, q, h.lam * cphf, h.rho * rsign * cphf, h.dm, acc);
+        }
+        {
+            const M3<float2> W = ll.load_smem(cur + LB);
+            float2 q[12];
+            load_spinor(in + (size_t)cyb * 12, q);
+            hop_body<-1>(W, q, h.lam * cphb, h.rho * rsign * cphb, h.dm, acc);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <int K, int SGN>
 BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, AccF &acc) {
     float2 p[12];
@@ -340,7 +385,7 @@ BRI_D void all_hops(std::integer_sequence<int, Js...>, const LL &ll, const typen
     (hop_pair<Js>(ll, in, site, nb, rsign, acc), ...);
 }
 
-template <class LL, bool PF>
+template <class LL, int VAR>
 __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out, Geom g,
                          double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
@@ -362,7 +407,13 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
     }
     const float rsign = mode == 1 ? -1.f : 1.f;
     if constexpr (sizeof(T) == 8) {
-        f32_hops<PF>(ll, in, site, nb, rsign, acc);
+        if constexpr (VAR == 2) {
+            extern __shared__ float4 lslots[];
+            const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 4u * LL::SLOTS * 16u;
+            f32_hops_cpasync(ll, in, site, nb, rsign, lbase, acc);
+        } else {
+            f32_hops<VAR == 1>(ll, in, site, nb, rsign, acc);
+        }
     } else {
         all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
     }
@@ -530,30 +581,40 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     const int variant = threads >> 11;
     threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads[2] = {0, 0};  // per-kernel limit from its register use
+    static int max_threads[3] = {0, 0, 0};  // per-kernel limit from its register use
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
-        const int v = variant == 1 ? 1 : 0;
+        const int v = variant == 1 ? 1 : variant == 2 ? 2 : 0;
         if (max_threads[v] == 0) {
             cudaFuncAttributes attr;
-            cudaError_t e = v ? cudaFuncGetAttributes(&attr, k_dslash<LL, true>)
-                              : cudaFuncGetAttributes(&attr, k_dslash<LL, false>);
+            cudaError_t e = v == 1 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 1>)
+                          : v == 2 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 2>)
+                                   : cudaFuncGetAttributes(&attr, k_dslash<LL, 0>);
             max_threads[v] = e == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+            if (v == 2) {
+                // per-thread link slots: 2 stages x 2 fields; allow up to 256 threads
+                cudaFuncSetAttribute(k_dslash<LL, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     256 * 4 * LL::SLOTS * 16);
+                if (max_threads[v] > 256) max_threads[v] = 256;
+            }
         }
         if (threads > max_threads[v]) threads = max_threads[v] & ~31;
         grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
-        if (v) k_dslash<LL, true><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
-        else k_dslash<LL, false><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        if (v == 1) k_dslash<LL, 1><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else if (v == 2)
+            k_dslash<LL, 2><<<grid, threads, threads * 4 * LL::SLOTS * 16, s>>>(mode, ll, (const T *)in, (T *)out, g,
+                                                                                 diag, skip);
+        else k_dslash<LL, 0><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
     } else {
         (void)variant;
         if (max_threads[0] == 0) {
             cudaFuncAttributes attr;
             max_threads[0] =
-                cudaFuncGetAttributes(&attr, k_dslash<LL, false>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+                cudaFuncGetAttributes(&attr, k_dslash<LL, 0>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
         }
         if (threads > max_threads[0]) threads = max_threads[0] & ~31;
         grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
-        k_dslash<LL, false><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        k_dslash<LL, 0><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
     }
 }
 

@@ -71,6 +71,27 @@ BRI_D M3<float2> from_eight(const float p[8]) {
     return m;
 }
 
+// asynchronous global -> shared copies of 16, 8 or 4 bytes (sm_80+ cp.async)
+BRI_D void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+BRI_D void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+BRI_D void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+BRI_D float4 lds4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+BRI_D uint4 lds4u(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
 struct LinkF64 {
     using T = double2;
     const double2 *__restrict__ h;
@@ -85,9 +106,39 @@ struct LinkF64 {
 
 template <bri_comp C> struct LinkF32 {
     using T = float2;
+    // 16-byte shared-memory slots one field occupies when prefetched
+    static constexpr int SLOTS = C == BRI_LINK_FULL ? 5 : C == BRI_LINK_2ROW ? 3 : 2;
     const float4 *__restrict__ a;
     const float2 *__restrict__ b;
     int V;
+    BRI_D void prefetch(int j, int site, uint32_t dst) const {
+        constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) cp_async16(dst + 16 * q, a + ((size_t)j * NQ + q) * V + site);
+        if (C == BRI_LINK_FULL) cp_async8(dst + 64, b + (size_t)j * V + site);
+    }
+    BRI_D M3<float2> load_smem(uint32_t src) const {
+        M3<float2> m;
+        if (C == BRI_LINK_8PARAM) {
+            float4 v0 = lds4(src), v1 = lds4(src + 16);
+            float p[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            return from_eight(p);
+        }
+        constexpr int NQ = C == BRI_LINK_FULL ? 4 : 3;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            float4 v = lds4(src + 16 * q);
+            m.e[2 * q] = make_float2(v.x, v.y);
+            m.e[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        if (C == BRI_LINK_FULL) {
+            float4 v = lds4(src + 64);
+            m.e[8] = make_float2(v.x, v.y);
+        } else {
+            third_row(m);
+        }
+        return m;
+    }
     BRI_D M3<float2> load(int j, int site) const {
         M3<float2> m;
         if (C == BRI_LINK_FULL) {
@@ -117,9 +168,42 @@ template <bri_comp C> struct LinkF32 {
 
 template <bri_comp C> struct LinkF16 {
     using T = float2;
+    static constexpr int SLOTS = C == BRI_LINK_FULL ? 3 : C == BRI_LINK_2ROW ? 2 : 1;
     const uint4 *__restrict__ a;
     const void *__restrict__ b;
     int V;
+    BRI_D void prefetch(int j, int site, uint32_t dst) const {
+        if (C == BRI_LINK_FULL) {
+            cp_async16(dst, a + ((size_t)j * 2) * V + site);
+            cp_async16(dst + 16, a + ((size_t)j * 2 + 1) * V + site);
+            cp_async4(dst + 32, (const uint32_t *)b + (size_t)j * V + site);
+        } else if (C == BRI_LINK_2ROW) {
+            cp_async16(dst, a + (size_t)j * V + site);
+            cp_async8(dst + 16, (const uint2 *)b + (size_t)j * V + site);
+        } else {
+            cp_async16(dst, a + (size_t)j * V + site);
+        }
+    }
+    BRI_D M3<float2> load_smem(uint32_t src) const {
+        M3<float2> m;
+        if (C == BRI_LINK_FULL) {
+            uint4 v = lds4u(src), w = lds4u(src + 16), t = lds4u(src + 32);
+            m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
+            m.e[4] = h2f(w.x); m.e[5] = h2f(w.y); m.e[6] = h2f(w.z); m.e[7] = h2f(w.w);
+            m.e[8] = h2f(t.x);
+        } else if (C == BRI_LINK_2ROW) {
+            uint4 v = lds4u(src), t = lds4u(src + 16);
+            m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
+            m.e[4] = h2f(t.x); m.e[5] = h2f(t.y);
+            third_row(m);
+        } else {
+            uint4 v = lds4u(src);
+            float2 q0 = h2f(v.x), q1 = h2f(v.y), q2 = h2f(v.z), q3 = h2f(v.w);
+            float p[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
+            m = from_eight(p);
+        }
+        return m;
+    }
     BRI_D M3<float2> load(int j, int site) const {
         M3<float2> m;
         if (C == BRI_LINK_FULL) {

@@ -128,9 +128,14 @@ def _det3_torch(M):
             + M[:, 0, 2] * (M[:, 1, 0] * M[:, 2, 1] - M[:, 1, 1] * M[:, 2, 0]))
 
 
+def _mm3(A, B):
+    """Batched 3x3 product as three broadcast multiply-adds (elementwise kernels)."""
+    return A[:, :, 0, None] * B[:, None, 0, :] + A[:, :, 1, None] * B[:, None, 1, :] + A[:, :, 2, None] * B[:, None, 2, :]
+
+
 def _expm_i_torch(X):
     """exp(X) for a batch of small anti-hermitian 3x3 matrices by Taylor series
-    with scaling and squaring (matmuls only)."""
+    with scaling and squaring (elementwise products only)."""
     import torch
 
     k = 6  # ||X|| / 64 is far below 1 for these inputs
@@ -139,10 +144,10 @@ def _expm_i_torch(X):
     E = eye.clone()
     term = eye.clone()
     for n in range(1, 13):
-        term = term @ Y / n
+        term = _mm3(term, Y) / n
         E = E + term
     for _ in range(k):
-        E = E @ E
+        E = _mm3(E, E)
     return E
 
 
@@ -162,7 +167,7 @@ def random_su3_links_torch(L, eps, seed, device="cuda", chunk=1 << 20):
         h = torch.randn((e - s, 8), generator=g, dtype=torch.float64, device=device)
         H = torch.einsum("na,aij->nij", h.to(torch.complex128), lam) / 2.0
         M = _expm_i_torch(1j * eps * H)
-        M = M @ (1.5 * torch.eye(3, dtype=M.dtype, device=device) - 0.5 * M.conj().transpose(1, 2) @ M)
+        M = _mm3(M, 1.5 * torch.eye(3, dtype=M.dtype, device=device) - 0.5 * _mm3(M.conj().transpose(1, 2), M))
         det = _det3_torch(M)
         U[s:e] = M / (det ** (1.0 / 3.0))[:, None, None]
     return U.reshape(V, 4, 3, 3)

@@ -95,6 +95,26 @@ def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f32", "2row"), ("f32", "8param"), ("f16", "full"),
+                                       ("f16", "2row"), ("f16", "8param")])
+def test_kernel_variants_agree(gpu, prec, comp):
+    """Every launch shape of the FP32-arithmetic stencil (plain kernel at several
+    block sizes, register link prefetch, cp.async link prefetch) performs the
+    same arithmetic: results are bitwise equal."""
+    L, bc = (6, 5, 4, 8), AP
+    U = synth.random_su3_links(L, 0.4, 41)
+    psi = synth.gaussian_spinor(L, 2, 42).astype(np.complex64)
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+    x = torch.as_tensor(psi, device=gpu)
+    outs = []
+    for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256):
+        op.set_threads(prec, 2, shape)
+        outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
+    for shape, o in outs[1:]:
+        assert torch.equal(o, outs[0][1]), shape
+
+
 def test_multi_rhs_equals_single(gpu):
     L, bc = (4, 3, 5, 4), AP
     U = synth.random_su3_links(L, 0.3, 5)
