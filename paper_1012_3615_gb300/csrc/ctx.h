@@ -25,6 +25,7 @@ struct bri_ctx {
     double2 *hops64 = nullptr;  // FP64 hops, [40][9][V]
     bool have64 = false;
     LinkStore f32, f16;
+    LinkStore p32, p16;  // site-pair interleaved copies (full / 2-row, even t extent)
     SolverWork *work = nullptr;
     std::map<std::string, int> tune;  // launch-shape cache: key -> threads per block
     std::string err;

@@ -10,6 +10,10 @@ namespace bri {
 template <class LL>
 void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
                    const int *skip, int threads, cudaStream_t s);
+// defined in dslash_pair.cuh, instantiated in dslash_pair_*.cu
+template <class PL>
+void dslash_pair_launch(int mode, const PL &pl, const void *in, void *out, int nrhs, const Geom &g, double diag,
+                        const int *skip, int threads, cudaStream_t s);
 }  // namespace bri
 
 using namespace bri;
@@ -41,6 +45,26 @@ bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, dou
     } else {
         const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
         if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
+        const LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
+        if ((threads >> 11) == 3 && ps.valid) {
+            // site-pair kernel on the interleaved copy
+            const int thr = (threads & 2047) ? (threads & 2047) : 64;
+            const int H = g.V / 2;
+            if (prec == BRI_F32) {
+                if (ps.comp == BRI_LINK_FULL)
+                    dslash_pair_launch(mode, PairF32<9>{(const float4 *)ps.a, H}, in, out, nrhs, g, diag, skip, thr, s);
+                else
+                    dslash_pair_launch(mode, PairF32<6>{(const float4 *)ps.a, H}, in, out, nrhs, g, diag, skip, thr, s);
+            } else {
+                if (ps.comp == BRI_LINK_FULL)
+                    dslash_pair_launch(mode, PairF16<9>{(const uint2 *)ps.a, H}, in, out, nrhs, g, diag, skip, thr, s);
+                else
+                    dslash_pair_launch(mode, PairF16<6>{(const uint2 *)ps.a, H}, in, out, nrhs, g, diag, skip, thr, s);
+            }
+            BRI_LAUNCHED(ctx);
+            return BRI_OK;
+        }
+        if ((threads >> 11) == 3) threads = 128;  // no pair copy for this storage: plain kernel
         if (prec == BRI_F32) {
             if (st.comp == BRI_LINK_FULL)
                 dslash_launch(mode, LinkF32<BRI_LINK_FULL>{(const float4 *)st.a, (const float2 *)st.b, g.V}, in, out, nrhs,

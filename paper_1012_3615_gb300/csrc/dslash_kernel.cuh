@@ -268,13 +268,16 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
 template <class LL>
 BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
                             uint32_t lbase, AccF &acc) {
-    constexpr uint32_t LB = LL::SLOTS * 16;  // bytes per field
+    // layout [stage][field][chunk][thread] of 16-byte slots; lbase = this thread's
+    // slot of stage 0, field 0, chunk 0
+    const uint32_t stride = 16u * blockDim.x;      // between chunks
+    const uint32_t LB = stride * LL::SLOTS;        // between the two fields of a stage
     HopConst hc = c_hop[0];
     int yf, yb;
     float phf, phb;
     hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
-    ll.prefetch(0, site, lbase);
-    ll.prefetch(0, yb, lbase + LB);
+    ll.prefetch(0, site, lbase, stride);
+    ll.prefetch(0, yb, lbase + LB, stride);
     asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll 1
     for (int j = 0; j < NCANON; j++) {
@@ -286,18 +289,18 @@ BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int sit
             hc = c_hop[j + 1];
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
             const uint32_t nxt = lbase + (uint32_t)((j + 1) & 1) * 2 * LB;
-            ll.prefetch(j + 1, site, nxt);
-            ll.prefetch(j + 1, yb, nxt + LB);
+            ll.prefetch(j + 1, site, nxt, stride);
+            ll.prefetch(j + 1, yb, nxt + LB, stride);
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;" ::: "memory");
         {
-            const M3<float2> W = ll.load_smem(cur);
+            const M3<float2> W = ll.load_smem(cur, stride);
             float2 q[12];
             load_spinor(in + (size_t)cyf * 12, q);
             hop_body<1>(W, q, h.lam * cphf, h.rho * rsign * cphf, h.dm, acc);
         }
         {
-            const M3<float2> W = ll.load_smem(cur + LB);
+            const M3<float2> W = ll.load_smem(cur + LB, stride);
             float2 q[12];
             load_spinor(in + (size_t)cyb * 12, q);
             hop_body<-1>(W, q, h.lam * cphb, h.rho * rsign * cphb, h.dm, acc);
@@ -409,7 +412,7 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
     if constexpr (sizeof(T) == 8) {
         if constexpr (VAR == 2) {
             extern __shared__ float4 lslots[];
-            const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 4u * LL::SLOTS * 16u;
+            const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 16u;
             f32_hops_cpasync(ll, in, site, nb, rsign, lbase, acc);
         } else {
             f32_hops<VAR == 1>(ll, in, site, nb, rsign, acc);

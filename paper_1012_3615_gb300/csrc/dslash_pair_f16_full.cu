@@ -1,0 +1,4 @@
+// Site-pair stencil kernel instantiated for the f16_full pair-interleaved format.
+#include "dslash_pair.cuh"
+
+BRI_INSTANTIATE_DSLASH_PAIR(bri::PairF16<9>)

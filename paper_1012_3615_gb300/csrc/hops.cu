@@ -138,6 +138,31 @@ template <bri_comp C> __global__ void k_store_f16(const double2 *__restrict__ h,
     }
 }
 
+// site-pair interleaved copies: entry e of field j for sites (i, i + V/2) as
+// (Re_i, Re_{i+V/2}, Im_i, Im_{i+V/2}); E = 9 (full) or 6 (2-row)
+template <int E> __global__ void k_store_pair_f32(const double2 *__restrict__ h, float4 *__restrict__ out, Geom g) {
+    const int H = g.V / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= H) return;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const double2 wa = h[((size_t)j * 9 + e) * g.V + i], wb = h[((size_t)j * 9 + e) * g.V + i + H];
+        out[((size_t)j * E + e) * H + i] = make_float4((float)wa.x, (float)wb.x, (float)wa.y, (float)wb.y);
+    }
+}
+template <int E> __global__ void k_store_pair_f16(const double2 *__restrict__ h, uint2 *__restrict__ out, Geom g) {
+    const int H = g.V / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= H) return;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const double2 wa = h[((size_t)j * 9 + e) * g.V + i], wb = h[((size_t)j * 9 + e) * g.V + i + H];
+        out[((size_t)j * E + e) * H + i] = make_uint2(pack_h2(wa.x, wb.x), pack_h2(wa.y, wb.y));
+    }
+}
+
 // [40][9][V] -> [V][40][9]
 __global__ void k_export_hops(const double2 *__restrict__ h, double2 *__restrict__ out, Geom g) {
     const int site = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,6 +225,8 @@ bri_status bri_hops_build_impl(bri_ctx *ctx, cudaStream_t s) {
     ctx->have64 = true;
     ctx->f32.valid = false;
     ctx->f16.valid = false;
+    ctx->p32.valid = false;
+    ctx->p16.valid = false;
     return BRI_OK;
 }
 
@@ -233,6 +260,28 @@ bri_status bri_hops_store_impl(bri_ctx *ctx, bri_prec prec, bri_comp comp, cudaS
     }
     BRI_LAUNCHED(ctx);
     st.valid = true;
+    // site-pair interleaved copy for the pair kernel (full and 2-row, even t extent)
+    LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
+    ps.valid = false;
+    if (comp != BRI_LINK_8PARAM && ctx->g.L[3] % 2 == 0) {
+        const int E = comp == BRI_LINK_FULL ? 9 : 6;
+        if (ps.a && ps.comp != comp) {
+            cudaFree(ps.a);
+            ps.a = nullptr;
+        }
+        if (!ps.a) BRI_TRY_CUDA(ctx, cudaMalloc(&ps.a, (prec == BRI_F32 ? 16 : 8) * (size_t)E * NCANON * (V / 2)));
+        ps.comp = comp;
+        dim3 pg((unsigned)((V / 2 + T - 1) / T), NCANON);
+        if (prec == BRI_F32) {
+            if (E == 9) k_store_pair_f32<9><<<pg, T, 0, s>>>(ctx->hops64, (float4 *)ps.a, ctx->g);
+            else k_store_pair_f32<6><<<pg, T, 0, s>>>(ctx->hops64, (float4 *)ps.a, ctx->g);
+        } else {
+            if (E == 9) k_store_pair_f16<9><<<pg, T, 0, s>>>(ctx->hops64, (uint2 *)ps.a, ctx->g);
+            else k_store_pair_f16<6><<<pg, T, 0, s>>>(ctx->hops64, (uint2 *)ps.a, ctx->g);
+        }
+        BRI_LAUNCHED(ctx);
+        ps.valid = true;
+    }
     return BRI_OK;
 }
 

@@ -111,28 +111,31 @@ template <bri_comp C> struct LinkF32 {
     const float4 *__restrict__ a;
     const float2 *__restrict__ b;
     int V;
-    BRI_D void prefetch(int j, int site, uint32_t dst) const {
+    // shared-memory slots are chunk-major across the block: chunk q of this
+    // thread's field at dst + q * stride (stride = 16 bytes x threads), so a
+    // warp's 16-byte accesses are consecutive and free of bank conflicts
+    BRI_D void prefetch(int j, int site, uint32_t dst, uint32_t stride) const {
         constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;
 #pragma unroll
-        for (int q = 0; q < NQ; q++) cp_async16(dst + 16 * q, a + ((size_t)j * NQ + q) * V + site);
-        if (C == BRI_LINK_FULL) cp_async8(dst + 64, b + (size_t)j * V + site);
+        for (int q = 0; q < NQ; q++) cp_async16(dst + stride * q, a + ((size_t)j * NQ + q) * V + site);
+        if (C == BRI_LINK_FULL) cp_async8(dst + stride * 4, b + (size_t)j * V + site);
     }
-    BRI_D M3<float2> load_smem(uint32_t src) const {
+    BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
         M3<float2> m;
         if (C == BRI_LINK_8PARAM) {
-            float4 v0 = lds4(src), v1 = lds4(src + 16);
+            float4 v0 = lds4(src), v1 = lds4(src + stride);
             float p[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             return from_eight(p);
         }
         constexpr int NQ = C == BRI_LINK_FULL ? 4 : 3;
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            float4 v = lds4(src + 16 * q);
+            float4 v = lds4(src + stride * q);
             m.e[2 * q] = make_float2(v.x, v.y);
             m.e[2 * q + 1] = make_float2(v.z, v.w);
         }
         if (C == BRI_LINK_FULL) {
-            float4 v = lds4(src + 64);
+            float4 v = lds4(src + stride * 4);
             m.e[8] = make_float2(v.x, v.y);
         } else {
             third_row(m);
@@ -172,27 +175,27 @@ template <bri_comp C> struct LinkF16 {
     const uint4 *__restrict__ a;
     const void *__restrict__ b;
     int V;
-    BRI_D void prefetch(int j, int site, uint32_t dst) const {
+    BRI_D void prefetch(int j, int site, uint32_t dst, uint32_t stride) const {
         if (C == BRI_LINK_FULL) {
             cp_async16(dst, a + ((size_t)j * 2) * V + site);
-            cp_async16(dst + 16, a + ((size_t)j * 2 + 1) * V + site);
-            cp_async4(dst + 32, (const uint32_t *)b + (size_t)j * V + site);
+            cp_async16(dst + stride, a + ((size_t)j * 2 + 1) * V + site);
+            cp_async4(dst + 2 * stride, (const uint32_t *)b + (size_t)j * V + site);
         } else if (C == BRI_LINK_2ROW) {
             cp_async16(dst, a + (size_t)j * V + site);
-            cp_async8(dst + 16, (const uint2 *)b + (size_t)j * V + site);
+            cp_async8(dst + stride, (const uint2 *)b + (size_t)j * V + site);
         } else {
             cp_async16(dst, a + (size_t)j * V + site);
         }
     }
-    BRI_D M3<float2> load_smem(uint32_t src) const {
+    BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
         M3<float2> m;
         if (C == BRI_LINK_FULL) {
-            uint4 v = lds4u(src), w = lds4u(src + 16), t = lds4u(src + 32);
+            uint4 v = lds4u(src), w = lds4u(src + stride), t = lds4u(src + 2 * stride);
             m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
             m.e[4] = h2f(w.x); m.e[5] = h2f(w.y); m.e[6] = h2f(w.z); m.e[7] = h2f(w.w);
             m.e[8] = h2f(t.x);
         } else if (C == BRI_LINK_2ROW) {
-            uint4 v = lds4u(src), t = lds4u(src + 16);
+            uint4 v = lds4u(src), t = lds4u(src + stride);
             m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
             m.e[4] = h2f(t.x); m.e[5] = h2f(t.y);
             third_row(m);
@@ -229,6 +232,43 @@ template <bri_comp C> struct LinkF16 {
             m = from_eight(p);
         }
         return m;
+    }
+};
+
+}  // namespace bri
+
+namespace bri {
+
+// ---- site-pair interleaved storage -------------------------------------------
+// For the pair kernel a thread owns sites i and i + V/2 (a translation by half
+// the t extent), and every packed register holds one quantity of both sites.
+// Field j, complex entry e of sites (i, i + V/2) is stored as
+// (Re_i, Re_{i+V/2}, Im_i, Im_{i+V/2}) at [j][e][V/2]: FP32 as one float4, FP16
+// as four halves (uint2).  Full storage keeps e = 0..8, 2-row e = 0..5.
+template <int E> struct PairF32 {
+    static constexpr int NE = E;
+    const float4 *__restrict__ a;
+    int H;  // V / 2
+    BRI_D void load(int j, int i, float2 R[E], float2 I[E]) const {
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const float4 v = a[((size_t)j * E + e) * H + i];
+            R[e] = make_float2(v.x, v.y);
+            I[e] = make_float2(v.z, v.w);
+        }
+    }
+};
+template <int E> struct PairF16 {
+    static constexpr int NE = E;
+    const uint2 *__restrict__ a;
+    int H;
+    BRI_D void load(int j, int i, float2 R[E], float2 I[E]) const {
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const uint2 v = a[((size_t)j * E + e) * H + i];
+            R[e] = h2f(v.x);
+            I[e] = h2f(v.y);
+        }
     }
 };
 

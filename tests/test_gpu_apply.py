@@ -115,6 +115,27 @@ def test_kernel_variants_agree(gpu, prec, comp):
         assert torch.equal(o, outs[0][1]), shape
 
 
+@pytest.mark.parametrize("prec,comp,tol", [("f32", "full", 1e-6), ("f32", "2row", 1e-6), ("f16", "full", 2e-3),
+                                           ("f16", "2row", 2e-3)])
+@pytest.mark.parametrize("L,bc", [((3, 5, 4, 6), AP), ((4, 4, 4, 4), PER), ((8, 4, 4, 8), AP)])
+def test_pair_kernel_matches_oracle(gpu, prec, comp, tol, L, bc):
+    """The site-pair kernel (two sites i, i + V/2 per thread, pair-interleaved
+    links) against the oracle for D, D^dagger and the overlap kernel."""
+    U, psi, W = _setup(L, bc, 50 + sum(L))
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+    x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
+    for shape in (6144 + 64, 6144 + 128):
+        op.set_threads(prec, 2, shape)
+        out = op.apply(x, m0=0.05, prec=prec).cpu().numpy()
+        outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
+        outh = op.overlap_kernel(x, rho=1.0, prec=prec).cpu().numpy()
+        for r in range(psi.shape[0]):
+            assert _rel_l2(out[r], oracle.apply(L, bc, W, 0.05, psi[r])) < tol
+            assert _rel_l2(outd[r], oracle.apply(L, bc, W, 0.05, psi[r], dagger=True)) < tol
+            assert _rel_l2(outh[r], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) < tol
+
+
 def test_multi_rhs_equals_single(gpu):
     L, bc = (4, 3, 5, 4), AP
     U = synth.random_su3_links(L, 0.3, 5)
