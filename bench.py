@@ -45,6 +45,46 @@ def site_bytes(mode, nrhs):
     return LINK_BYTES[mode] + nrhs * spinor_bytes(mode)
 
 
+KERNEL_SOURCES = ["paper_1012_3615_gb300/csrc/dslash_kernel.cuh", "paper_1012_3615_gb300/csrc/dslash_pair.cuh",
+                  "paper_1012_3615_gb300/csrc/links.cuh", "paper_1012_3615_gb300/csrc/common.cuh"]
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x (FMA = 2) x max SM clock
+
+
+def kernel_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(mode, nrhs, shape, lattice):
+    """DRAM bytes per launch of the apply kernel from the committed ncu summary
+    (profiles/dslash_traffic.json), if it was taken on the current kernel
+    sources with the same storage mode, RHS count and launch shape; else None.
+    A capture on a smaller lattice is scaled by the number of sites."""
+    p = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    for e in d.get("captures", []):
+        if e.get("mode") == mode and e.get("nrhs") == nrhs and e.get("launch_shape") == shape:
+            v_cap = 1
+            for t in e["lattice"]:
+                v_cap *= t
+            v = 1
+            for t in lattice:
+                v *= t
+            return e["dram_bytes_per_launch"] * v / v_cap
+    return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -300,9 +340,15 @@ def native(args, world, rank, local, pg):
                    "l2": "inputs larger than L2 (hopping fields %.1f GB)" % (LINK_BYTES[mode] * V / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": dslash_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": dslash_gbs / peak, "traffic": None,
+                     "frac": dslash_gbs / peak,
+                     "traffic": measured_traffic(mode, nrhs, op.threads(prec, nrhs), L),
                      "peak_kind": peak_kind + " hbm_gbs (copy)",
-                     "algorithmic_bytes_per_launch": bytes_step, "tflops": flops},
+                     "algorithmic_bytes_per_launch": bytes_step, "tflops": flops,
+                     "alu": {"achieved_tflops": flops, "peak_tflops": FP32_PEAK_TFLOPS if prec != "f64" else 1.25,
+                             "frac": flops / (FP32_PEAK_TFLOPS if prec != "f64" else 1.25),
+                             "peak_kind": "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec != "f64"
+                             else "FP64 nominal 1.25 TFLOP/s"},
+                     "kernel_hash": kernel_hash()},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": ck,

@@ -140,6 +140,14 @@ BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, c
             A[3 * c + cp] = w;
             B[3 * c + cp] = make_float2(-w.y, w.x);
         }
+    // +-r SGN d_mu per direction, formed once per hop
+    float cp_[4], cn_[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        const float c = dm[mu] > 0 ? (float)SGN * r : -(float)SGN * r;
+        cp_[mu] = c;
+        cn_[mu] = -c;
+    }
 #pragma unroll
     for (int sp = 0; sp < 4; sp++) {
         float2 chi[3];
@@ -160,7 +168,61 @@ BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, c
             if (dm[mu] == 0) continue;  // uniform across the warp
             const int s = gcol(mu, sp);
             const int gr = gre(mu, s), gi = gim(mu, s);
-            const float cf = r * (float)(SGN * dm[mu] * (gr != 0 ? gr : gi));
+            const float cf = (gr != 0 ? gr : gi) > 0 ? cp_[mu] : cn_[mu];  // sign is compile-time
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.a[3 * s + c]);
+                else acc.ai[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.ai[3 * s + c]);
+            }
+        }
+    }
+}
+
+
+template <int SGN>
+BRI_D void hop_body_w(const M3<float2> &W, const float2 p[12], float l, float r, const int dm[4], AccF &acc) {
+    // entries (re, im) of the matrix, re and im each used as a broadcast
+    // coefficient against the spinor and against i times the spinor
+    float wr[9], wi[9];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) {
+            wr[3 * c + cp] = SGN > 0 ? W.e[3 * c + cp].x : W.e[3 * cp + c].x;
+            wi[3 * c + cp] = SGN > 0 ? W.e[3 * c + cp].y : -W.e[3 * cp + c].y;
+        }
+    // +-r SGN d_mu per direction, formed once per hop
+    float cp_[4], cn_[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        const float c = dm[mu] > 0 ? (float)SGN * r : -(float)SGN * r;
+        cp_[mu] = c;
+        cn_[mu] = -c;
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        float2 chi[3];
+        float2 ip[3];  // i psi
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) ip[cp] = make_float2(-p[3 * sp + cp].y, p[3 * sp + cp].x);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 t = __fmul2_rn(f2(wr[3 * c]), p[3 * sp]);
+            t = __ffma2_rn(f2(wi[3 * c]), ip[0], t);
+            t = __ffma2_rn(f2(wr[3 * c + 1]), p[3 * sp + 1], t);
+            t = __ffma2_rn(f2(wi[3 * c + 1]), ip[1], t);
+            t = __ffma2_rn(f2(wr[3 * c + 2]), p[3 * sp + 2], t);
+            t = __ffma2_rn(f2(wi[3 * c + 2]), ip[2], t);
+            chi[c] = t;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc.a[3 * sp + c] = __ffma2_rn(f2(l), chi[c], acc.a[3 * sp + c]);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (dm[mu] == 0) continue;  // uniform across the warp
+            const int s = gcol(mu, sp);
+            const int gr = gre(mu, s), gi = gim(mu, s);
+            const float cf = (gr != 0 ? gr : gi) > 0 ? cp_[mu] : cn_[mu];  // sign is compile-time
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.a[3 * s + c]);
@@ -206,10 +268,30 @@ BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &p
 // FP32 stencil over the 40 (d, -d) pairs as a compact loop.  PF = true loads
 // the two links of pair j + 1 while pair j is computed (links stream from
 // DRAM; the neighbour spinors mostly hit L1/L2).
-template <bool PF, class LL>
+template <bool PF, int BODY, class LL>
 BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
                     AccF &acc) {
-    if constexpr (!PF) {
+    if constexpr (!PF && BODY == 1) {
+#pragma unroll 1
+        for (int j = 0; j < NCANON; j++) {
+            const HopConst hc = c_hop[j];
+            int yf, yb;
+            float phf, phb;
+            hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+            {
+                M3<float2> W = ll.load(j, site);
+                float2 q[12];
+                load_spinor(in + (size_t)yf * 12, q);
+                hop_body_w<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
+            }
+            {
+                M3<float2> W = ll.load(j, yb);
+                float2 q[12];
+                load_spinor(in + (size_t)yb * 12, q);
+                hop_body_w<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
+            }
+        }
+    } else if constexpr (!PF) {
 #pragma unroll 1
         for (int j = 0; j < NCANON; j++) {
             const HopConst hc = c_hop[j];
@@ -415,7 +497,7 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
             const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 16u;
             f32_hops_cpasync(ll, in, site, nb, rsign, lbase, acc);
         } else {
-            f32_hops<VAR == 1>(ll, in, site, nb, rsign, acc);
+            f32_hops<VAR == 1, VAR == 4 ? 1 : 0>(ll, in, site, nb, rsign, acc);
         }
     } else {
         all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
@@ -584,14 +666,15 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     const int variant = threads >> 11;
     threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads[3] = {0, 0, 0};  // per-kernel limit from its register use
+    static int max_threads[5] = {0, 0, 0, 0, 0};  // per-kernel limit from its register use
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
-        const int v = variant == 1 ? 1 : variant == 2 ? 2 : 0;
+        const int v = (variant == 1 || variant == 2 || variant == 4) ? variant : 0;
         if (max_threads[v] == 0) {
             cudaFuncAttributes attr;
             cudaError_t e = v == 1 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 1>)
                           : v == 2 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 2>)
+                          : v == 4 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 4>)
                                    : cudaFuncGetAttributes(&attr, k_dslash<LL, 0>);
             max_threads[v] = e == cudaSuccess ? attr.maxThreadsPerBlock : 128;
             if (v == 2) {
@@ -604,6 +687,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         if (threads > max_threads[v]) threads = max_threads[v] & ~31;
         grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
         if (v == 1) k_dslash<LL, 1><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else if (v == 4) k_dslash<LL, 4><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 2)
             k_dslash<LL, 2><<<grid, threads, threads * 4 * LL::SLOTS * 16, s>>>(mode, ll, (const T *)in, (T *)out, g,
                                                                                  diag, skip);

@@ -50,6 +50,13 @@ BRI_D void pair_hop(const float2 R[9], const float2 I[9], const float2 *__restri
 #pragma unroll
     for (int e = 0; e < 9; e++) NI[e] = pneg(I[e]);
     const float2 nr = pneg(r);
+    // coefficient of direction mu for a +1 gamma entry (and its negative)
+    float2 cpos[4], cneg[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        cpos[mu] = SGN * dm[mu] > 0 ? r : nr;
+        cneg[mu] = SGN * dm[mu] > 0 ? nr : r;
+    }
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         // spins 2 half, 2 half + 1 of the two neighbour spinors (48 bytes each)
@@ -89,9 +96,9 @@ BRI_D void pair_hop(const float2 R[9], const float2 I[9], const float2 *__restri
                 if (dm[mu] == 0) continue;  // uniform across the warp
                 const int s = gcol(mu, sp);
                 const int gr = gre(mu, s), gi = gim(mu, s);
-                const int sg = SGN * dm[mu] * (gr != 0 ? gr : gi);
-                const float2 cf = sg > 0 ? r : nr;
-                const float2 ncf = sg > 0 ? nr : r;
+                const int g = gr != 0 ? gr : gi;  // compile-time sign
+                const float2 cf = g > 0 ? cpos[mu] : cneg[mu];
+                const float2 ncf = g > 0 ? cneg[mu] : cpos[mu];
                 if (gr != 0) {
                     acc.r[3 * s + c] = __ffma2_rn(cf, cr, acc.r[3 * s + c]);
                     acc.i[3 * s + c] = __ffma2_rn(cf, ci, acc.i[3 * s + c]);

@@ -99,8 +99,8 @@ def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
                                        ("f16", "2row"), ("f16", "8param")])
 def test_kernel_variants_agree(gpu, prec, comp):
     """Every launch shape of the FP32-arithmetic stencil (plain kernel at several
-    block sizes, register link prefetch, cp.async link prefetch) performs the
-    same arithmetic: results are bitwise equal."""
+    block sizes, register link prefetch, cp.async link prefetch, broadcast-link
+    arithmetic) computes the same result to FP32 rounding."""
     L, bc = (6, 5, 4, 8), AP
     U = synth.random_su3_links(L, 0.4, 41)
     psi = synth.gaussian_spinor(L, 2, 42).astype(np.complex64)
@@ -108,11 +108,12 @@ def test_kernel_variants_agree(gpu, prec, comp):
     op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
     x = torch.as_tensor(psi, device=gpu)
     outs = []
-    for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256):
+    for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256, 8192 + 128, 8192 + 256):
         op.set_threads(prec, 2, shape)
         outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
     for shape, o in outs[1:]:
-        assert torch.equal(o, outs[0][1]), shape
+        err = (torch.linalg.vector_norm(o - outs[0][1]) / torch.linalg.vector_norm(outs[0][1])).item()
+        assert err < 1e-6, (shape, err)
 
 
 @pytest.mark.parametrize("prec,comp,tol", [("f32", "full", 1e-6), ("f32", "2row", 1e-6), ("f16", "full", 2e-3),
