@@ -204,7 +204,7 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * the cp.async shared-memory link-prefetch variant (at most 256 threads),
  * adding 6144 the site-pair kernel (two sites per thread, full and 2-row
  * storage with an even t extent; otherwise the plain kernel), adding 8192 the
- * plain kernel with link entries as broadcast operands.
+ * plain kernel without the separate accumulator for the +-i gamma entries.
  * bri_get_threads returns
  * the current choice (untuned: 0 where the tiled kernel applies, else 128) or
  * a negative bri_status. */

@@ -140,14 +140,6 @@ BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, c
             A[3 * c + cp] = w;
             B[3 * c + cp] = make_float2(-w.y, w.x);
         }
-    // +-r SGN d_mu per direction, formed once per hop
-    float cp_[4], cn_[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        const float c = dm[mu] > 0 ? (float)SGN * r : -(float)SGN * r;
-        cp_[mu] = c;
-        cn_[mu] = -c;
-    }
 #pragma unroll
     for (int sp = 0; sp < 4; sp++) {
         float2 chi[3];
@@ -168,7 +160,7 @@ BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, c
             if (dm[mu] == 0) continue;  // uniform across the warp
             const int s = gcol(mu, sp);
             const int gr = gre(mu, s), gi = gim(mu, s);
-            const float cf = (gr != 0 ? gr : gi) > 0 ? cp_[mu] : cn_[mu];  // sign is compile-time
+            const float cf = r * (float)(SGN * dm[mu] * (gr != 0 ? gr : gi));
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.a[3 * s + c]);
@@ -179,40 +171,30 @@ BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, c
 }
 
 
+// Variant of hop_body without the separate accumulator for the +-i gamma
+// entries: i chi is formed where it is needed (fewer registers, more moves).
 template <int SGN>
 BRI_D void hop_body_w(const M3<float2> &W, const float2 p[12], float l, float r, const int dm[4], AccF &acc) {
-    // entries (re, im) of the matrix, re and im each used as a broadcast
-    // coefficient against the spinor and against i times the spinor
-    float wr[9], wi[9];
+    float2 A[9], B[9];
 #pragma unroll
     for (int c = 0; c < 3; c++)
 #pragma unroll
         for (int cp = 0; cp < 3; cp++) {
-            wr[3 * c + cp] = SGN > 0 ? W.e[3 * c + cp].x : W.e[3 * cp + c].x;
-            wi[3 * c + cp] = SGN > 0 ? W.e[3 * c + cp].y : -W.e[3 * cp + c].y;
+            const float2 w = SGN > 0 ? W.e[3 * c + cp] : make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
+            A[3 * c + cp] = w;
+            B[3 * c + cp] = make_float2(-w.y, w.x);
         }
-    // +-r SGN d_mu per direction, formed once per hop
-    float cp_[4], cn_[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        const float c = dm[mu] > 0 ? (float)SGN * r : -(float)SGN * r;
-        cp_[mu] = c;
-        cn_[mu] = -c;
-    }
 #pragma unroll
     for (int sp = 0; sp < 4; sp++) {
         float2 chi[3];
-        float2 ip[3];  // i psi
-#pragma unroll
-        for (int cp = 0; cp < 3; cp++) ip[cp] = make_float2(-p[3 * sp + cp].y, p[3 * sp + cp].x);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            float2 t = __fmul2_rn(f2(wr[3 * c]), p[3 * sp]);
-            t = __ffma2_rn(f2(wi[3 * c]), ip[0], t);
-            t = __ffma2_rn(f2(wr[3 * c + 1]), p[3 * sp + 1], t);
-            t = __ffma2_rn(f2(wi[3 * c + 1]), ip[1], t);
-            t = __ffma2_rn(f2(wr[3 * c + 2]), p[3 * sp + 2], t);
-            t = __ffma2_rn(f2(wi[3 * c + 2]), ip[2], t);
+            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
+            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
+            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
+            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
+            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
+            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
             chi[c] = t;
         }
 #pragma unroll
@@ -222,16 +204,15 @@ BRI_D void hop_body_w(const M3<float2> &W, const float2 p[12], float l, float r,
             if (dm[mu] == 0) continue;  // uniform across the warp
             const int s = gcol(mu, sp);
             const int gr = gre(mu, s), gi = gim(mu, s);
-            const float cf = (gr != 0 ? gr : gi) > 0 ? cp_[mu] : cn_[mu];  // sign is compile-time
+            const float cf = r * (float)(SGN * dm[mu] * (gr != 0 ? gr : gi));
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.a[3 * s + c]);
-                else acc.ai[3 * s + c] = __ffma2_rn(f2(cf), chi[c], acc.ai[3 * s + c]);
+                const float2 z = gr != 0 ? chi[c] : make_float2(-chi[c].y, chi[c].x);
+                acc.a[3 * s + c] = __ffma2_rn(f2(cf), z, acc.a[3 * s + c]);
             }
         }
     }
 }
-
 
 // Per-field constants of the 40 canonical offsets (offset, class weights and
 // the offset within the shared-memory halo tile), read from the constant cache

@@ -99,8 +99,8 @@ def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
                                        ("f16", "2row"), ("f16", "8param")])
 def test_kernel_variants_agree(gpu, prec, comp):
     """Every launch shape of the FP32-arithmetic stencil (plain kernel at several
-    block sizes, register link prefetch, cp.async link prefetch, broadcast-link
-    arithmetic) computes the same result to FP32 rounding."""
+    block sizes, register link prefetch, cp.async link prefetch, fewer-register
+    form) computes the same result to FP32 rounding."""
     L, bc = (6, 5, 4, 8), AP
     U = synth.random_su3_links(L, 0.4, 41)
     psi = synth.gaussian_spinor(L, 2, 42).astype(np.complex64)
