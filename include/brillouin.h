@@ -200,7 +200,7 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * down to a multiple of 32, clamped to the kernel's limit at launch), or 0 for
  * the shared-memory tiled kernel (FP32 spinors; extents multiples of
  * 8, 4, 2, 2; otherwise 0 falls back to 128 threads).  Adding 2048 selects
- * the register link-prefetch variant of the plain FP32 kernel, adding 4096
+ * the L2 link-prefetch variant of the plain FP32 kernel, adding 4096
  * the cp.async shared-memory link-prefetch variant (at most 256 threads),
  * adding 6144 the site-pair kernel (two sites per thread, full and 2-row
  * storage with an even t extent; otherwise the plain kernel), adding 8192 the

@@ -246,9 +246,9 @@ BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &p
     }
 }
 
-// FP32 stencil over the 40 (d, -d) pairs as a compact loop.  PF = true loads
-// the two links of pair j + 1 while pair j is computed (links stream from
-// DRAM; the neighbour spinors mostly hit L1/L2).
+// FP32 stencil over the 40 (d, -d) pairs as a compact loop.  PF = true also
+// prefetches the two links of pair j + 2 into L2 (the links stream from DRAM;
+// the neighbour spinors mostly hit L1/L2).
 template <bool PF, int BODY, class LL>
 BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
                     AccF &acc) {
@@ -293,32 +293,32 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
             }
         }
     } else {
-        HopConst hc = c_hop[0];
-        int yf, yb;
-        float phf, phb;
-        hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
-        M3<float2> Wf = ll.load(0, site), Wb = ll.load(0, yb);
-#pragma unroll 2
+        // the links of pair j + 2 are prefetched into L2 while pair j is computed
+#pragma unroll 1
         for (int j = 0; j < NCANON; j++) {
-            const HopConst h = hc;
-            const int cyf = yf, cyb = yb;
-            const float cphf = phf, cphb = phb;
-            const M3<float2> Wf0 = Wf, Wb0 = Wb;
-            if (j + 1 < NCANON) {
-                hc = c_hop[j + 1];
-                hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
-                Wf = ll.load(j + 1, site);
-                Wb = ll.load(j + 1, yb);
+            if (j + 2 < NCANON) {
+                const HopConst hp = c_hop[j + 2];
+                int pyf, pyb;
+                float pphf, pphb;
+                hop_nb(hp.dm, site, nb, pyf, pphf, pyb, pphb);
+                ll.prefetch_field_l2(j + 2, site);
+                ll.prefetch_field_l2(j + 2, pyb);
+            }
+            const HopConst hc = c_hop[j];
+            int yf, yb;
+            float phf, phb;
+            hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+            {
+                M3<float2> W = ll.load(j, site);
+                float2 q[12];
+                load_spinor(in + (size_t)yf * 12, q);
+                hop_body<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
             }
             {
+                M3<float2> W = ll.load(j, yb);
                 float2 q[12];
-                load_spinor(in + (size_t)cyf * 12, q);
-                hop_body<1>(Wf0, q, h.lam * cphf, h.rho * rsign * cphf, h.dm, acc);
-            }
-            {
-                float2 q[12];
-                load_spinor(in + (size_t)cyb * 12, q);
-                hop_body<-1>(Wb0, q, h.lam * cphb, h.rho * rsign * cphb, h.dm, acc);
+                load_spinor(in + (size_t)yb * 12, q);
+                hop_body<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
             }
         }
     }

@@ -92,6 +92,9 @@ BRI_D uint4 lds4u(uint32_t a) {
     return v;
 }
 
+// L2 prefetch of one 16-byte chunk (brings the line to L2, no register cost)
+BRI_D void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 struct LinkF64 {
     using T = double2;
     const double2 *__restrict__ h;
@@ -119,6 +122,12 @@ template <bri_comp C> struct LinkF32 {
 #pragma unroll
         for (int q = 0; q < NQ; q++) cp_async16(dst + stride * q, a + ((size_t)j * NQ + q) * V + site);
         if (C == BRI_LINK_FULL) cp_async8(dst + stride * 4, b + (size_t)j * V + site);
+    }
+    BRI_D void prefetch_field_l2(int j, int site) const {
+        constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) prefetch_l2(a + ((size_t)j * NQ + q) * V + site);
+        if (C == BRI_LINK_FULL) prefetch_l2(b + (size_t)j * V + site);
     }
     BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
         M3<float2> m;
@@ -185,6 +194,18 @@ template <bri_comp C> struct LinkF16 {
             cp_async8(dst + stride, (const uint2 *)b + (size_t)j * V + site);
         } else {
             cp_async16(dst, a + (size_t)j * V + site);
+        }
+    }
+    BRI_D void prefetch_field_l2(int j, int site) const {
+        if (C == BRI_LINK_FULL) {
+            prefetch_l2(a + ((size_t)j * 2) * V + site);
+            prefetch_l2(a + ((size_t)j * 2 + 1) * V + site);
+            prefetch_l2((const uint32_t *)b + (size_t)j * V + site);
+        } else if (C == BRI_LINK_2ROW) {
+            prefetch_l2(a + (size_t)j * V + site);
+            prefetch_l2((const uint2 *)b + (size_t)j * V + site);
+        } else {
+            prefetch_l2(a + (size_t)j * V + site);
         }
     }
     BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
