@@ -282,7 +282,7 @@ def native(args, world, rank, local, pg):
     out = torch.empty_like(x)
     if args.threads is not None:
         op.set_threads(prec, nrhs, args.threads)
-    else:
+    elif args.tune:
         op.tune(prec, nrhs)
     stream = torch.cuda.current_stream()
     time_apply(op, x, out, mode, nrhs, 1, args.warmup, stream)  # warm-up (untimed)
@@ -375,11 +375,69 @@ def native(args, world, rank, local, pg):
                 del xx, oo
         line["sweep"] = sweep
     if args.solve:
-        del op, x, out
         torch.cuda.empty_cache()
         line["solve"] = solve_bench(args, dev)
+    if args.rows:
+        torch.cuda.empty_cache()
+        line["rows"] = rows_bench(dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def rows_bench(dev):
+    """Timings of the other rows of the path, on their own workloads:
+    hop precompute (path sums + SU(3) projection, FP64) on 32^3x64 and 8^4,
+    the FP64 apply on 8^4 (the parity workload, 10 applies), and the fermion
+    force d Re(chi^dagger D psi)/dU plus d(phi^dagger (D^dagger D)^-1 phi)/dU on 12^4."""
+    import torch
+
+    from paper_1012_3615_gb300 import Brillouin, synth
+
+    out = {}
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    for L, eps in (((32, 32, 32, 64), 0.3), ((8, 8, 8, 8), 0.3)):
+        U = synth.random_su3_links_torch(L, eps, SEED + 7, device=dev)
+        op = Brillouin(L, BC)
+        op.build_hops(U)  # warm-up (allocations)
+        ms, _ = timed(lambda: op.build_hops(U))
+        V = synth.volume(L)
+        out["hop_precompute_%s" % "x".join(map(str, L))] = {
+            "ms": ms, "projections_per_s": 36 * V / (ms * 1e-3), "sites": V}
+        if L == (8, 8, 8, 8):
+            psi = synth.gaussian_spinor_torch(L, 1, SEED + 8, device=dev)
+            o = torch.empty_like(psi)
+            op.apply(psi, 0.0, out=o)
+            ms, _ = timed(lambda: op.apply(psi, 0.0, out=o), reps=10)
+            out["apply_fp64_8x8x8x8"] = {"ms": ms, "GB/s": site_bytes("f64-full", 1) * V / (ms * 1e-3) / 1e9,
+                                          "TFLOP/s": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e12}
+        del op, U
+        torch.cuda.empty_cache()
+    L = (12, 12, 12, 12)
+    U = synth.random_su3_links_torch(L, 0.3, SEED + 9, device=dev)
+    op = Brillouin(L, BC)
+    op.build_hops(U)
+    chi, psi = synth.gaussian_spinor_torch(L, 2, SEED + 10, device=dev)
+    chi, psi = chi.contiguous(), psi.contiguous()
+    op.force(chi, psi)
+    ms, _ = timed(lambda: op.force(chi, psi))
+    out["force_12x12x12x12"] = {"ms": ms}
+    t0 = time.perf_counter()
+    dU, info = op.force_inverse(chi, m0=0.0, tol=1e-10)
+    torch.cuda.synchronize()
+    out["force_inverse_12x12x12x12"] = {"seconds": time.perf_counter() - t0, "iters_second_solve": info["iters"],
+                                        "status": info["status"]}
+    return out
 
 
 def solve_bench(args, dev):
@@ -458,10 +516,12 @@ def main():
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--solve", action="store_true", help="add the solver workloads (time to 1e-10)")
     ap.add_argument("--solve-small", action="store_true", help="only the 16^3x32 solver workload")
+    ap.add_argument("--rows", action="store_true", help="add hop precompute, FP64 apply and force timings")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lattice", type=lambda t: [int(v) for v in t.split(",")], default=None,
                     help="lattice extents x,y,z,t (default 32,32,32,64)")
+    ap.add_argument("--tune", action="store_true", help="run the launch-shape tuner before timing")
     ap.add_argument("--threads", type=int, default=None,
                     help="fixed launch shape (threads per block; 0 = shared-memory tiled kernel); skips the tuner")
     args = ap.parse_args()

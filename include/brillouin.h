@@ -205,9 +205,8 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * adding 6144 the site-pair kernel (two sites per thread, full and 2-row
  * storage with an even t extent; otherwise the plain kernel), adding 8192 the
  * plain kernel without the separate accumulator for the +-i gamma entries.
- * bri_get_threads returns
- * the current choice (untuned: 0 where the tiled kernel applies, else 128) or
- * a negative bri_status. */
+ * bri_get_threads returns the current choice (untuned: 128 for BRI_F64,
+ * 128 + 2048 otherwise) or a negative bri_status. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 

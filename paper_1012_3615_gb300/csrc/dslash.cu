@@ -26,12 +26,14 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
     return buf;
 }
 
-// launch shape: threads per block of the plain kernel, or 0 for the
-// shared-memory tiled kernel (FP32 spinors, extents multiples of the tile)
+// launch shape (threads per block, kernel variant in bits 11+; see
+// bri_set_threads).  Untuned default: FP64 -> unrolled kernel, 128 threads;
+// FP32 arithmetic -> hop loop with L2 link prefetch, 128 threads (the fastest
+// shape measured on 32^3x64 and 16^3x32).
 int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
     auto it = ctx->tune.find(bri_tune_key(ctx, prec, nrhs));
     if (it != ctx->tune.end()) return it->second;
-    return (prec != BRI_F64 && tiled_ok(ctx->g)) ? 0 : 128;
+    return prec == BRI_F64 ? 128 : (128 | 2048);
 }
 
 bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,

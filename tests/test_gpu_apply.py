@@ -13,8 +13,8 @@ AP = (1, 1, 1, -1)
 PER = (1, 1, 1, 1)
 
 CASES = [((4, 4, 4, 4), AP), ((3, 5, 4, 6), AP), ((4, 3, 3, 4), PER), ((3, 3, 3, 3), AP)]
-# extents that are multiples of the shared-memory tile (8, 4, 2, 2): FP32 applies
-# there use the tiled kernel by default
+# extents that are multiples of the shared-memory tile (8, 4, 2, 2), where the
+# tiled kernel can be selected
 TILED = [((8, 4, 4, 4), AP), ((16, 8, 6, 4), PER)]
 
 
@@ -87,7 +87,7 @@ def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
     op = Brillouin(L, bc)
     op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
     x = torch.as_tensor(psi, device=gpu)
-    assert op.threads(prec, 3) == 0  # tiled by default here
+    op.set_threads(prec, 3, 0)  # tiled kernel
     tiled = [op.apply(x, 0.1, prec=prec), op.apply(x, 0.1, dagger=True, prec=prec), op.overlap_kernel(x, 1.0, prec=prec)]
     op.set_threads(prec, 3, 128)
     plain = [op.apply(x, 0.1, prec=prec), op.apply(x, 0.1, dagger=True, prec=prec), op.overlap_kernel(x, 1.0, prec=prec)]
@@ -205,7 +205,6 @@ def test_full_size_sampled_sites(gpu):
     psi = synth.gaussian_spinor_torch(L, 1, 1016, device=gpu)
     op = Brillouin(L, bc)
     op.build_hops(U, prec="f32", comp="full")
-    op.tune("f32", 1)
     out64 = op.apply(psi, 0.0, prec="f64")
     out32 = op.apply(psi.to(torch.complex64), 0.0, prec="f32")
     rng = np.random.default_rng(11)
