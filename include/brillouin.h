@@ -189,6 +189,26 @@ bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, voi
  * than 4096 sites), BRI_ECUDA. */
 bri_status bri_build_hops_noalloc(const bri_lattice *lat, const double *U, double *W, void *stream);
 
+/* result[0] + i result[1] = <a, b> = sum conj(a) b over nrhs spinor fields
+ * (the dot product of the Krylov solvers, FP64 accumulation: per-block partial
+ * sums added in block order, deterministic).  a, b: device, [nrhs][V][4][3]
+ * complex in the storage of prec; result: host, 2 doubles.  Synchronises the
+ * stream.  Errors: BRI_EINVAL. */
+bri_status bri_cdot(bri_ctx *ctx, double *result, const void *a, const void *b, int nrhs, bri_prec prec,
+                    void *stream);
+
+/* Class weights of the operator (Sec. 8): D(x, x+d) = s_d(x) [lambda_n +
+ * rho_n sum_mu d_mu gamma_mu] (x) W_d(x) for n = |d|_1 = 1..4 and
+ * D(x, x) = m0 + lambda_0.  The default is the der_iso / lap_bri column of
+ * Tab. rholambda (the Brillouin operator); the other columns (Wilson:
+ * lambda = (4, -1/2, 0, 0, 0), rho_1 = 1/2; the hypercube operator) or any
+ * other member of the class can be set.  Classes with lambda_n = rho_n = 0
+ * are skipped by the apply.  lambda, rho: host arrays of 5 doubles (rho[0]
+ * ignored).  Applies to every later apply, solve and force on ctx.
+ * Errors: BRI_EINVAL (null or non-finite weights). */
+bri_status bri_set_weights(bri_ctx *ctx, const double *lambda, const double *rho);
+bri_status bri_get_weights(bri_ctx *ctx, double *lambda, double *rho);
+
 /* Tune the launch shape of the apply kernels for (prec, nrhs) on this
  * lattice (timed with CUDA events, result cached in the context and, when the
  * environment variable BRI_TUNE_CACHE names a file, in that file).

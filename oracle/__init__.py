@@ -84,6 +84,18 @@ def weights():
     return lam, rho
 
 
+def set_weights(lam, rho):
+    """Replace the class weights (lambda_0..4, rho_0..4; rho_0 ignored)."""
+    la = np.ascontiguousarray(lam, dtype=np.float64)
+    ra = np.ascontiguousarray(rho, dtype=np.float64)
+    lib().bo_set_weights(_p(la), _p(ra))
+
+
+def reset_weights():
+    """Restore the der_iso / lap_bri column of Tab. rholambda."""
+    lib().bo_reset_weights()
+
+
 def gamma(mu):
     """Dense 4x4 gamma_mu (mu=0..3) or gamma_5 (mu=4)."""
     g = np.zeros((4, 4), np.complex128)

@@ -109,14 +109,36 @@ static int hop_class(const int d[4]) {
 }
 
 /* ------------------------------------------------------------------ */
-/* weights: Tab. "rholambda", columns der_iso and lap_bri              */
+/* weights: Tab. "rholambda" (default: columns der_iso and lap_bri)     */
 /* ------------------------------------------------------------------ */
-int bo_weights(double lam[5], double rho[5]) {
+/* The operator's class weights; bo_set_weights replaces them (other columns of
+ * Tab. rholambda, e.g. Wilson's), bo_reset_weights restores the table's
+ * der_iso / lap_bri column. */
+static double g_lam[5], g_rho[5];
+static int g_weights_set = 0;
+int bo_reset_weights(void) {
     static const double lam_num[5] = {240, -8, -4, -2, -1}; /* / 128 */
     static const double rho_num[5] = {0, 64, 16, 4, 1};     /* / 432 */
     for (int n = 0; n < 5; n++) {
-        lam[n] = lam_num[n] / 128.0;
-        rho[n] = rho_num[n] / 432.0;
+        g_lam[n] = lam_num[n] / 128.0;
+        g_rho[n] = rho_num[n] / 432.0;
+    }
+    g_weights_set = 1;
+    return 0;
+}
+int bo_set_weights(const double lam[5], const double rho[5]) {
+    for (int n = 0; n < 5; n++) {
+        g_lam[n] = lam[n];
+        g_rho[n] = n == 0 ? 0.0 : rho[n];
+    }
+    g_weights_set = 1;
+    return 0;
+}
+int bo_weights(double lam[5], double rho[5]) {
+    if (!g_weights_set) bo_reset_weights();
+    for (int n = 0; n < 5; n++) {
+        lam[n] = g_lam[n];
+        rho[n] = g_rho[n];
     }
     return 0;
 }

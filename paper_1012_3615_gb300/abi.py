@@ -48,6 +48,9 @@ SIGNATURES = {
                                   ctypes.POINTER(bri_solve_info), c_void_p]),
     "bri_project_su3": (c_int, [c_void_p, c_void_p, c_void_p, c_long, c_void_p]),
     "bri_build_hops_noalloc": (c_int, [ctypes.POINTER(bri_lattice), c_void_p, c_void_p, c_void_p]),
+    "bri_cdot": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "bri_set_weights": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "bri_get_weights": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "bri_tune": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "bri_set_threads": (c_int, [c_void_p, c_int, c_int, c_int]),
     "bri_get_threads": (c_int, [c_void_p, c_int, c_int]),

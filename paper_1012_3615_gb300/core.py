@@ -13,6 +13,15 @@ _PREC = {"f64": abi.BRI_F64, "f32": abi.BRI_F32, "f16": abi.BRI_F16}
 _COMP = {"full": abi.BRI_LINK_FULL, "2row": abi.BRI_LINK_2ROW, "8param": abi.BRI_LINK_8PARAM}
 
 
+# Columns of Tab. rholambda: (lambda_0..4, rho_0..4)
+WEIGHTS = {
+    "brillouin": ([240 / 128, -8 / 128, -4 / 128, -2 / 128, -1 / 128], [0, 64 / 432, 16 / 432, 4 / 432, 1 / 432]),
+    "wilson": ([4.0, -0.5, 0, 0, 0], [0, 0.5, 0, 0, 0]),
+    "hypercube": ([1.852720547, -0.060757866, -0.030036032, -0.015967620, -0.008426812],
+                  [0, 0.136846794, 0.032077284, 0.011058131, 0.004748991]),
+}
+
+
 class BriError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (abi.STATUS_NAMES.get(status, status), msg))
@@ -128,6 +137,47 @@ class Brillouin:
         self._check(self.lib.bri_force_inverse(self.ctx, _ptr(dU), _ptr(phi), float(m0), float(tol), int(maxit),
                                                ctypes.byref(info), _stream()))
         return dU, info.as_dict()
+
+    def cdot(self, a, b, prec="f64"):
+        """<a, b> = sum conj(a) b (FP64 accumulation in the library)."""
+        n = self._spinor(a, prec)
+        self._spinor(b, prec)
+        r = (ctypes.c_double * 2)()
+        self._check(self.lib.bri_cdot(self.ctx, r, _ptr(a), _ptr(b), n, _PREC[prec], _stream()))
+        return complex(r[0], r[1])
+
+    def max_eig_ddag_d(self, iters=60, m0=0.0, prec="f32", seed=0):
+        """Largest eigenvalue of D^dagger D by power iteration (applies and dot
+        products in the library); returns the last Rayleigh quotient."""
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed)
+        dt = spinor_dtype(prec)
+        rdt = torch.float64 if dt == torch.complex128 else torch.float32
+        x = torch.complex(torch.randn((1, self.V, 4, 3), generator=g, device="cuda", dtype=rdt),
+                          torch.randn((1, self.V, 4, 3), generator=g, device="cuda", dtype=rdt))
+        y = torch.empty_like(x)
+        lam = 0.0
+        for _ in range(iters):
+            nx = self.cdot(x, x, prec).real ** 0.5
+            x = x / nx
+            self.apply(x, m0, prec=prec, out=y)
+            z = self.apply(y, m0, dagger=True, prec=prec)
+            lam = self.cdot(x, z, prec).real
+            x = z
+        return lam
+
+    # ---- weights of the rho/lambda class (Sec. 8, Tab. rholambda) -------------
+    def set_weights(self, lam, rho):
+        """lam: lambda_0..4, rho: rho_0..4 (rho_0 ignored)."""
+        la = (ctypes.c_double * 5)(*[float(v) for v in lam])
+        ra = (ctypes.c_double * 5)(*[float(v) for v in rho])
+        self._check(self.lib.bri_set_weights(self.ctx, la, ra))
+
+    def weights(self):
+        la = (ctypes.c_double * 5)()
+        ra = (ctypes.c_double * 5)()
+        self._check(self.lib.bri_get_weights(self.ctx, la, ra))
+        return list(la), list(ra)
 
     def tune(self, prec="f32", nrhs=1):
         self._check(self.lib.bri_tune(self.ctx, _PREC[prec], int(nrhs), _stream()))

@@ -2,6 +2,7 @@
 // management, the launch-shape tuner and dispatch to the kernels.
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <fstream>
 #include <sstream>
@@ -76,6 +77,14 @@ bri_status bri_create(const bri_lattice *lat, bri_ctx **out) {
         ctx->g.bc[mu] = lat->bc_sign[mu];
     }
     ctx->g.V = (int)V;
+    {
+        double lam[5], rho[5];
+        for (int n = 0; n < 5; n++) {
+            lam[n] = lambda_w(n);
+            rho[n] = rho_w(n);
+        }
+        geom_set_weights(ctx->g, lam, rho);
+    }
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         delete ctx;
         return bri_fail(nullptr, BRI_ECUDA, "no CUDA device");
@@ -223,6 +232,36 @@ bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, voi
     if (n < 0 || (n > 0 && (!Y || !A || !bri_aligned16(Y) || !bri_aligned16(A))))
         return bri_fail(ctx, BRI_EINVAL, "A and Y must be 16-byte aligned device pointers, n >= 0");
     return bri_project_impl(ctx, (double2 *)Y, (const double2 *)A, n, as_stream(stream));
+}
+
+bri_status bri_cdot(bri_ctx *ctx, double *result, const void *a, const void *b, int nrhs, bri_prec prec,
+                    void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!result || !a || !b || !bri_aligned16(a) || !bri_aligned16(b))
+        return bri_fail(ctx, BRI_EINVAL, "result must be a host pointer, a and b 16-byte aligned device pointers");
+    if (nrhs < 1) return bri_fail(ctx, BRI_EINVAL, "nrhs must be >= 1");
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    return bri_cdot_impl(ctx, result, a, b, (size_t)ctx->g.V * 12 * nrhs, prec, as_stream(stream));
+}
+
+bri_status bri_set_weights(bri_ctx *ctx, const double *lambda, const double *rho) {
+    if (!ctx) return BRI_EINVAL;
+    if (!lambda || !rho) return bri_fail(ctx, BRI_EINVAL, "null weights");
+    for (int n = 0; n < 5; n++)
+        if (!std::isfinite(lambda[n]) || (n > 0 && !std::isfinite(rho[n])))
+            return bri_fail(ctx, BRI_EINVAL, "weights must be finite");
+    geom_set_weights(ctx->g, lambda, rho);
+    return BRI_OK;
+}
+
+bri_status bri_get_weights(bri_ctx *ctx, double *lambda, double *rho) {
+    if (!ctx) return BRI_EINVAL;
+    if (!lambda || !rho) return bri_fail(ctx, BRI_EINVAL, "null weights");
+    for (int n = 0; n < 5; n++) {
+        lambda[n] = ctx->g.lamd[n];
+        rho[n] = ctx->g.rhod[n];
+    }
+    return BRI_OK;
 }
 
 bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream) {

@@ -123,11 +123,23 @@ template <typename T> BRI_HD M3<T> m3_eye() {
 }
 
 // ---- geometry ---------------------------------------------------------------
+// Lattice geometry and the class weights of the operator (lambda_0..4,
+// rho_0..4 with rho_0 unused; by default the der_iso / lap_bri weights above).
 struct Geom {
     int L[4];
     int bc[4];
     int V;
+    float lam[5], rho[5];
+    double lamd[5], rhod[5];
 };
+inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) {
+    for (int n = 0; n < 5; n++) {
+        g.lamd[n] = lam[n];
+        g.rhod[n] = n == 0 ? 0.0 : rho[n];
+        g.lam[n] = (float)g.lamd[n];
+        g.rho[n] = (float)g.rhod[n];
+    }
+}
 
 // Per-site neighbour deltas (with periodic wrap) and boundary phases.
 struct SiteNb {

@@ -74,6 +74,8 @@ int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs);
 bri_status bri_export_hops_impl(bri_ctx *ctx, double2 *out, cudaStream_t s);
 void bri_solver_free(bri_ctx *ctx);
+bri_status bri_cdot_impl(bri_ctx *ctx, double *res, const void *a, const void *b, size_t n, bri_prec prec,
+                         cudaStream_t user);
 bri_status bri_dp_levels(bri_ctx *ctx, void *A, const int *klist, const int start[6], cudaStream_t s);
 bri_status bri_force_impl(bri_ctx *ctx, double2 *dU, const double2 *chi, const double2 *psi, cudaStream_t s);
 bri_status bri_solve_impl(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol, int maxit,

@@ -39,7 +39,7 @@ int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
 bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
                           const int *skip, int threads, cudaStream_t s) {
     const Geom &g = ctx->g;
-    const double diag = m0 + lambda_w(0);
+    const double diag = m0 + g.lamd[0];
     if (prec == BRI_F64) {
         if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "FP64 hopping fields not built");
         LinkF64 ll{ctx->hops64, g.V};

@@ -81,10 +81,10 @@ BRI_D float2 f2(float v) { return make_float2(v, v); }
 // FP32 hop with packed FMAs: chi = W psi as sum_c' (psi.re * w + psi.im * (i w));
 // p is the neighbour spinor, already loaded
 template <int K, int SGN>
-BRI_D void hop_apply_p(const M3<float2> &W, const float2 p[12], float ph, float rsign, AccF &acc) {
+BRI_D void hop_apply_p(const M3<float2> &W, const float2 p[12], float ph, float rsign, const Geom &g, AccF &acc) {
     constexpr int n = off_class(K);
-    const float l = (float)lambda_w(n) * ph;
-    const float r = (float)rho_w(n) * (ph * rsign);
+    const float l = g.lam[n] * ph;
+    const float r = g.rho[n] * (ph * rsign);
     float2 A[9], B[9];  // matrix entries w and i w (w = W or W^dagger entry)
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -219,15 +219,14 @@ BRI_D void hop_body_w(const M3<float2> &W, const float2 p[12], float l, float r,
 // with a warp-uniform index.
 struct HopConst {
     int dm[4];
-    float lam, rho;
+    int n;  // hop class |d|_1
     int hd;
 };
 BRI_HD constexpr HopConst make_hop(int j) {
     const int k = canon_k(j);
     const int n = off_class(k);
     return HopConst{{off_comp(k, 0), off_comp(k, 1), off_comp(k, 2), off_comp(k, 3)},
-                    (float)lambda_w(n),
-                    (float)rho_w(n),
+                    n,
                     off_comp(k, 0) + (TX + 2) * (off_comp(k, 1) + (TY + 2) * (off_comp(k, 2) + (TZ + 2) * off_comp(k, 3)))};
 }
 #define BRI_H4(j) make_hop(j), make_hop(j + 1), make_hop(j + 2), make_hop(j + 3)
@@ -251,11 +250,12 @@ BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &p
 // the neighbour spinors mostly hit L1/L2).
 template <bool PF, int BODY, class LL>
 BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
-                    AccF &acc) {
+                    const Geom &g, AccF &acc) {
     if constexpr (!PF && BODY == 1) {
 #pragma unroll 1
         for (int j = 0; j < NCANON; j++) {
             const HopConst hc = c_hop[j];
+            if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
             int yf, yb;
             float phf, phb;
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
@@ -263,19 +263,20 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 M3<float2> W = ll.load(j, site);
                 float2 q[12];
                 load_spinor(in + (size_t)yf * 12, q);
-                hop_body_w<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
+                hop_body_w<1>(W, q, g.lam[hc.n] * phf, g.rho[hc.n] * rsign * phf, hc.dm, acc);
             }
             {
                 M3<float2> W = ll.load(j, yb);
                 float2 q[12];
                 load_spinor(in + (size_t)yb * 12, q);
-                hop_body_w<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
+                hop_body_w<-1>(W, q, g.lam[hc.n] * phb, g.rho[hc.n] * rsign * phb, hc.dm, acc);
             }
         }
     } else if constexpr (!PF) {
 #pragma unroll 1
         for (int j = 0; j < NCANON; j++) {
             const HopConst hc = c_hop[j];
+            if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
             int yf, yb;
             float phf, phb;
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
@@ -283,13 +284,13 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 M3<float2> W = ll.load(j, site);
                 float2 q[12];
                 load_spinor(in + (size_t)yf * 12, q);
-                hop_body<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
+                hop_body<1>(W, q, g.lam[hc.n] * phf, g.rho[hc.n] * rsign * phf, hc.dm, acc);
             }
             {
                 M3<float2> W = ll.load(j, yb);
                 float2 q[12];
                 load_spinor(in + (size_t)yb * 12, q);
-                hop_body<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
+                hop_body<-1>(W, q, g.lam[hc.n] * phb, g.rho[hc.n] * rsign * phb, hc.dm, acc);
             }
         }
     } else {
@@ -305,6 +306,7 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 ll.prefetch_field_l2(j + 2, pyb);
             }
             const HopConst hc = c_hop[j];
+            if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
             int yf, yb;
             float phf, phb;
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
@@ -312,13 +314,13 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 M3<float2> W = ll.load(j, site);
                 float2 q[12];
                 load_spinor(in + (size_t)yf * 12, q);
-                hop_body<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
+                hop_body<1>(W, q, g.lam[hc.n] * phf, g.rho[hc.n] * rsign * phf, hc.dm, acc);
             }
             {
                 M3<float2> W = ll.load(j, yb);
                 float2 q[12];
                 load_spinor(in + (size_t)yb * 12, q);
-                hop_body<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
+                hop_body<-1>(W, q, g.lam[hc.n] * phb, g.rho[hc.n] * rsign * phb, hc.dm, acc);
             }
         }
     }
@@ -330,7 +332,7 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
 // costs no registers.  lbase: this thread's slots (2 stages x 2 links).
 template <class LL>
 BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
-                            uint32_t lbase, AccF &acc) {
+                            const Geom &g, uint32_t lbase, AccF &acc) {
     // layout [stage][field][chunk][thread] of 16-byte slots; lbase = this thread's
     // slot of stage 0, field 0, chunk 0
     const uint32_t stride = 16u * blockDim.x;      // between chunks
@@ -360,35 +362,37 @@ BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int sit
             const M3<float2> W = ll.load_smem(cur, stride);
             float2 q[12];
             load_spinor(in + (size_t)cyf * 12, q);
-            hop_body<1>(W, q, h.lam * cphf, h.rho * rsign * cphf, h.dm, acc);
+            hop_body<1>(W, q, g.lam[h.n] * cphf, g.rho[h.n] * rsign * cphf, h.dm, acc);
         }
         {
             const M3<float2> W = ll.load_smem(cur + LB, stride);
             float2 q[12];
             load_spinor(in + (size_t)cyb * 12, q);
-            hop_body<-1>(W, q, h.lam * cphb, h.rho * rsign * cphb, h.dm, acc);
+            hop_body<-1>(W, q, g.lam[h.n] * cphb, g.rho[h.n] * rsign * cphb, h.dm, acc);
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 template <int K, int SGN>
-BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, AccF &acc) {
+BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, const Geom &g,
+                     AccF &acc) {
     float2 p[12];
     load_spinor(psi, p);
-    hop_apply_p<K, SGN>(W, p, ph, rsign, acc);
+    hop_apply_p<K, SGN>(W, p, ph, rsign, g, acc);
 }
 
 // one hop: offset of hypercube index K, reversed when SGN = -1 (then W is the
 // dagger of the stored field)
 template <int K, int SGN>
-BRI_D void hop_apply(const M3<double2> &W, const double2 *__restrict__ psi, float ph, float rsign, AccD &accd) {
+BRI_D void hop_apply(const M3<double2> &W, const double2 *__restrict__ psi, float ph, float rsign, const Geom &g,
+                     AccD &accd) {
     using T = double2;
     using R = double;
     T *acc = accd.a;
     constexpr int n = off_class(K);
-    const R l = (R)lambda_w(n) * (R)ph;
-    const R r = (R)rho_w(n) * (R)(ph * rsign);
+    const R l = (R)g.lamd[n] * (R)ph;
+    const R r = (R)g.rhod[n] * (R)(ph * rsign);
     T p[12];
     load_spinor(psi, p);
 #pragma unroll
@@ -428,27 +432,29 @@ BRI_D void hop_apply(const M3<double2> &W, const double2 *__restrict__ psi, floa
 
 template <int J, class LL>
 BRI_D void hop_pair(const LL &ll, const typename LL::T *__restrict__ in, int site, const SiteNb &nb,
-                    float rsign, typename AccOf<typename LL::T>::A &acc) {
+                    float rsign, const Geom &g, typename AccOf<typename LL::T>::A &acc) {
     using T = typename LL::T;
     constexpr int K = canon_k(J);
+    if (g.lamd[off_class(K)] == 0.0 && g.rhod[off_class(K)] == 0.0) return;  // class not in the operator
     {
         float ph;
         const int y = nb_index<K, 1>(nb, site, ph);
         M3<T> W = ll.load(J, site);
-        hop_apply<K, 1>(W, in + (size_t)y * 12, ph, rsign, acc);
+        hop_apply<K, 1>(W, in + (size_t)y * 12, ph, rsign, g, acc);
     }
     {
         float ph;
         const int y = nb_index<K, -1>(nb, site, ph);
         M3<T> W = ll.load(J, y);
-        hop_apply<K, -1>(W, in + (size_t)y * 12, ph, rsign, acc);
+        hop_apply<K, -1>(W, in + (size_t)y * 12, ph, rsign, g, acc);
     }
 }
 
 template <class LL, int... Js>
 BRI_D void all_hops(std::integer_sequence<int, Js...>, const LL &ll, const typename LL::T *__restrict__ in,
-                    int site, const SiteNb &nb, float rsign, typename AccOf<typename LL::T>::A &acc) {
-    (hop_pair<Js>(ll, in, site, nb, rsign, acc), ...);
+                    int site, const SiteNb &nb, float rsign, const Geom &g,
+                    typename AccOf<typename LL::T>::A &acc) {
+    (hop_pair<Js>(ll, in, site, nb, rsign, g, acc), ...);
 }
 
 template <class LL, int VAR>
@@ -476,12 +482,12 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
         if constexpr (VAR == 2) {
             extern __shared__ float4 lslots[];
             const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 16u;
-            f32_hops_cpasync(ll, in, site, nb, rsign, lbase, acc);
+            f32_hops_cpasync(ll, in, site, nb, rsign, g, lbase, acc);
         } else {
-            f32_hops<VAR == 1, VAR == 4 ? 1 : 0>(ll, in, site, nb, rsign, acc);
+            f32_hops<VAR == 1, VAR == 4 ? 1 : 0>(ll, in, site, nb, rsign, g, acc);
         }
     } else {
-        all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, acc);
+        all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, g, acc);
     }
     T p[12];
     load_spinor(in + (size_t)site * 12, p);
@@ -584,6 +590,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, 
 #pragma unroll 1
     for (int j = 0; j < NCANON; j++) {
         const HopConst h = c_hop[j];
+        if (g.lam[h.n] == 0.f && g.rho[h.n] == 0.f) continue;  // class not in the operator
         int yf, yb;
         float phf, phb;
         hop_nb(h.dm, site, nb, yf, phf, yb, phb);
@@ -591,13 +598,13 @@ __global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, 
             M3<float2> W = ll.load(j, site);
             float2 q[12];
             lds_spinor(sbase + (uint32_t)((hc + h.hd) * SSTR * 16), q);
-            hop_body<1>(W, q, h.lam * phf, h.rho * rsign * phf, h.dm, acc);
+            hop_body<1>(W, q, g.lam[h.n] * phf, g.rho[h.n] * rsign * phf, h.dm, acc);
         }
         {
             M3<float2> W = ll.load(j, yb);
             float2 q[12];
             lds_spinor(sbase + (uint32_t)((hc - h.hd) * SSTR * 16), q);
-            hop_body<-1>(W, q, h.lam * phb, h.rho * rsign * phb, h.dm, acc);
+            hop_body<-1>(W, q, g.lam[h.n] * phb, g.rho[h.n] * rsign * phb, h.dm, acc);
         }
     }
     float2 p[12];

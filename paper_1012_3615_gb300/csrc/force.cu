@@ -35,7 +35,7 @@ __global__ void k_hop_grad(const double2 *__restrict__ chi, const double2 *__res
     if (site >= g.V) return;
     const int k = canon_k(j);
     const int n = off_class(k);
-    const double lam = lambda_w(n), rho = rho_w(n);
+    const double lam = g.lamd[n], rho = g.rhod[n];
     int x[4];
     SiteNb nb = site_nb(g, site, x);
     int d[4];

@@ -276,6 +276,25 @@ __global__ void k_accum64(double2 *x, const float2 *e, const double *nrm, const 
         x[o + i] = make_double2(x[o + i].x + sc * v.x, x[o + i].y + sc * v.y);
     }
 }
+// <a, b> = sum conj(a) b over n complex elements, FP64 accumulation; the last
+// block writes the result to out[0..1]
+template <typename T>
+__global__ void k_cdot(const T *a, const T *b, size_t n, double *out, double *part, unsigned *tick) {
+    double acc[2] = {0, 0};
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+        T x = a[i], y = b[i];
+        acc[0] += (double)x.x * y.x + (double)x.y * y.y;
+        acc[1] += (double)x.x * y.y - (double)x.y * y.x;
+    }
+    if (partial_and_ticket<2>(acc, part, tick) && threadIdx.x == 0) {
+        double q[2];
+        gather_partials<2>(part, q);
+        out[0] = q[0];
+        out[1] = q[1];
+        tick[0] = 0;
+    }
+}
+
 template <typename T> __global__ void k_zero(T *x, size_t n) {
     for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) x[i] = mk<T>(0, 0);
 }
@@ -609,4 +628,20 @@ bri_status bri_solve_impl(bri_ctx *ctx, double *x, const double *b, int nrhs, do
     }
     if (!user) BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     return worst;
+}
+
+// complex dot product of two device vectors of n complex elements (FP64 or FP32
+// storage), FP64 accumulation; result to the host (synchronises the stream)
+bri_status bri_cdot_impl(bri_ctx *ctx, double *res, const void *a, const void *b, size_t n, bri_prec prec,
+                         cudaStream_t user) {
+    BRI_RETURN_IF(ensure_work(ctx, 1, false, false));
+    SolverWork *w = ctx->work;
+    cudaStream_t s = user ? user : w->own;
+    if (!user) BRI_TRY_CUDA(ctx, cudaDeviceSynchronize());
+    if (prec == BRI_F64) k_cdot<double2><<<RBLK, RT, 0, s>>>((const double2 *)a, (const double2 *)b, n, w->nrm, w->part, w->tick);
+    else k_cdot<float2><<<RBLK, RT, 0, s>>>((const float2 *)a, (const float2 *)b, n, w->nrm, w->part, w->tick);
+    BRI_LAUNCHED(ctx);
+    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(res, w->nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    return BRI_OK;
 }
