@@ -123,14 +123,31 @@ template <typename T> BRI_HD M3<T> m3_eye() {
 }
 
 // ---- geometry ---------------------------------------------------------------
+// Tile shape of the shared-memory stencil kernel (sites per CTA along x, y, z, t).
+constexpr int TX = 8, TY = 4, TZ = 2, TT = 2;
+
+// One (d, -d) hop pair of the stencil: offset d, stored field index j, the
+// class weights of |d|_1 and the offset of d within the shared-memory halo tile.
+struct HopArg {
+    int dm[4];
+    int j;
+    int hd;
+    float lam, rho;
+};
+
 // Lattice geometry and the class weights of the operator (lambda_0..4,
 // rho_0..4 with rho_0 unused; by default the der_iso / lap_bri weights above).
+// hop[0..nhop) lists the hop pairs whose class has a nonzero weight, in
+// canonical order; the FP32/FP16 stencils loop over it (kernel parameter
+// space, read with a warp-uniform index).
 struct Geom {
     int L[4];
     int bc[4];
     int V;
     float lam[5], rho[5];
     double lamd[5], rhod[5];
+    int nhop;
+    HopArg hop[NCANON];
 };
 inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) {
     for (int n = 0; n < 5; n++) {
@@ -138,6 +155,17 @@ inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) 
         g.rhod[n] = n == 0 ? 0.0 : rho[n];
         g.lam[n] = (float)g.lamd[n];
         g.rho[n] = (float)g.rhod[n];
+    }
+    g.nhop = 0;
+    for (int j = 0; j < NCANON; j++) {
+        const int k = canon_k(j), n = off_class(k);
+        if (g.lamd[n] == 0.0 && g.rhod[n] == 0.0) continue;
+        HopArg &h = g.hop[g.nhop++];
+        for (int mu = 0; mu < 4; mu++) h.dm[mu] = off_comp(k, mu);
+        h.j = j;
+        h.hd = h.dm[0] + (TX + 2) * (h.dm[1] + (TY + 2) * (h.dm[2] + (TZ + 2) * h.dm[3]));
+        h.lam = g.lam[n];
+        h.rho = g.rho[n];
     }
 }
 

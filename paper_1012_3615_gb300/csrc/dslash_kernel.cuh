@@ -214,26 +214,6 @@ BRI_D void hop_body_w(const M3<float2> &W, const float2 p[12], float l, float r,
     }
 }
 
-// Per-field constants of the 40 canonical offsets (offset, class weights and
-// the offset within the shared-memory halo tile), read from the constant cache
-// with a warp-uniform index.
-struct HopConst {
-    int dm[4];
-    int n;  // hop class |d|_1
-    int hd;
-};
-BRI_HD constexpr HopConst make_hop(int j) {
-    const int k = canon_k(j);
-    const int n = off_class(k);
-    return HopConst{{off_comp(k, 0), off_comp(k, 1), off_comp(k, 2), off_comp(k, 3)},
-                    n,
-                    off_comp(k, 0) + (TX + 2) * (off_comp(k, 1) + (TY + 2) * (off_comp(k, 2) + (TZ + 2) * off_comp(k, 3)))};
-}
-#define BRI_H4(j) make_hop(j), make_hop(j + 1), make_hop(j + 2), make_hop(j + 3)
-static __constant__ HopConst c_hop[NCANON] = {BRI_H4(0),  BRI_H4(4),  BRI_H4(8),  BRI_H4(12), BRI_H4(16),
-                                              BRI_H4(20), BRI_H4(24), BRI_H4(28), BRI_H4(32), BRI_H4(36)};
-#undef BRI_H4
-
 // neighbour index and boundary phase of the forward (d) and reversed (-d) hop
 BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &phf, int &yb, float &phb) {
     yf = yb = site;
@@ -253,9 +233,9 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                     const Geom &g, AccF &acc) {
     if constexpr (!PF && BODY == 1) {
 #pragma unroll 1
-        for (int j = 0; j < NCANON; j++) {
-            const HopConst hc = c_hop[j];
-            if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
+        for (int t = 0; t < g.nhop; t++) {
+            const HopArg hc = g.hop[t];
+            const int j = hc.j;
             int yf, yb;
             float phf, phb;
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
@@ -263,20 +243,20 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 M3<float2> W = ll.load(j, site);
                 float2 q[12];
                 load_spinor(in + (size_t)yf * 12, q);
-                hop_body_w<1>(W, q, g.lam[hc.n] * phf, g.rho[hc.n] * rsign * phf, hc.dm, acc);
+                hop_body_w<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
             }
             {
                 M3<float2> W = ll.load(j, yb);
                 float2 q[12];
                 load_spinor(in + (size_t)yb * 12, q);
-                hop_body_w<-1>(W, q, g.lam[hc.n] * phb, g.rho[hc.n] * rsign * phb, hc.dm, acc);
+                hop_body_w<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
             }
         }
     } else if constexpr (!PF) {
 #pragma unroll 1
-        for (int j = 0; j < NCANON; j++) {
-            const HopConst hc = c_hop[j];
-            if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
+        for (int t = 0; t < g.nhop; t++) {
+            const HopArg hc = g.hop[t];
+            const int j = hc.j;
             int yf, yb;
             float phf, phb;
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
@@ -284,29 +264,29 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 M3<float2> W = ll.load(j, site);
                 float2 q[12];
                 load_spinor(in + (size_t)yf * 12, q);
-                hop_body<1>(W, q, g.lam[hc.n] * phf, g.rho[hc.n] * rsign * phf, hc.dm, acc);
+                hop_body<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
             }
             {
                 M3<float2> W = ll.load(j, yb);
                 float2 q[12];
                 load_spinor(in + (size_t)yb * 12, q);
-                hop_body<-1>(W, q, g.lam[hc.n] * phb, g.rho[hc.n] * rsign * phb, hc.dm, acc);
+                hop_body<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
             }
         }
     } else {
-        // the links of pair j + 2 are prefetched into L2 while pair j is computed
+        // the links of pair t + 2 are prefetched into L2 while pair t is computed
 #pragma unroll 1
-        for (int j = 0; j < NCANON; j++) {
-            if (j + 2 < NCANON) {
-                const HopConst hp = c_hop[j + 2];
+        for (int t = 0; t < g.nhop; t++) {
+            if (t + 2 < g.nhop) {
+                const HopArg hp = g.hop[t + 2];
                 int pyf, pyb;
                 float pphf, pphb;
                 hop_nb(hp.dm, site, nb, pyf, pphf, pyb, pphb);
-                ll.prefetch_field_l2(j + 2, site);
-                ll.prefetch_field_l2(j + 2, pyb);
+                ll.prefetch_field_l2(hp.j, site);
+                ll.prefetch_field_l2(hp.j, pyb);
             }
-            const HopConst hc = c_hop[j];
-            if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
+            const HopArg hc = g.hop[t];
+            const int j = hc.j;
             int yf, yb;
             float phf, phb;
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
@@ -314,13 +294,13 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
                 M3<float2> W = ll.load(j, site);
                 float2 q[12];
                 load_spinor(in + (size_t)yf * 12, q);
-                hop_body<1>(W, q, g.lam[hc.n] * phf, g.rho[hc.n] * rsign * phf, hc.dm, acc);
+                hop_body<1>(W, q, hc.lam * phf, hc.rho * rsign * phf, hc.dm, acc);
             }
             {
                 M3<float2> W = ll.load(j, yb);
                 float2 q[12];
                 load_spinor(in + (size_t)yb * 12, q);
-                hop_body<-1>(W, q, g.lam[hc.n] * phb, g.rho[hc.n] * rsign * phb, hc.dm, acc);
+                hop_body<-1>(W, q, hc.lam * phb, hc.rho * rsign * phb, hc.dm, acc);
             }
         }
     }
@@ -337,38 +317,39 @@ BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int sit
     // slot of stage 0, field 0, chunk 0
     const uint32_t stride = 16u * blockDim.x;      // between chunks
     const uint32_t LB = stride * LL::SLOTS;        // between the two fields of a stage
-    HopConst hc = c_hop[0];
+    if (g.nhop == 0) return;
+    HopArg hc = g.hop[0];
     int yf, yb;
     float phf, phb;
     hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
-    ll.prefetch(0, site, lbase, stride);
-    ll.prefetch(0, yb, lbase + LB, stride);
+    ll.prefetch(hc.j, site, lbase, stride);
+    ll.prefetch(hc.j, yb, lbase + LB, stride);
     asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll 1
-    for (int j = 0; j < NCANON; j++) {
-        const HopConst h = hc;
+    for (int t = 0; t < g.nhop; t++) {
+        const HopArg h = hc;
         const int cyf = yf, cyb = yb;
         const float cphf = phf, cphb = phb;
-        const uint32_t cur = lbase + (uint32_t)(j & 1) * 2 * LB;
-        if (j + 1 < NCANON) {
-            hc = c_hop[j + 1];
+        const uint32_t cur = lbase + (uint32_t)(t & 1) * 2 * LB;
+        if (t + 1 < g.nhop) {
+            hc = g.hop[t + 1];
             hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
-            const uint32_t nxt = lbase + (uint32_t)((j + 1) & 1) * 2 * LB;
-            ll.prefetch(j + 1, site, nxt, stride);
-            ll.prefetch(j + 1, yb, nxt + LB, stride);
+            const uint32_t nxt = lbase + (uint32_t)((t + 1) & 1) * 2 * LB;
+            ll.prefetch(hc.j, site, nxt, stride);
+            ll.prefetch(hc.j, yb, nxt + LB, stride);
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;" ::: "memory");
         {
             const M3<float2> W = ll.load_smem(cur, stride);
             float2 q[12];
             load_spinor(in + (size_t)cyf * 12, q);
-            hop_body<1>(W, q, g.lam[h.n] * cphf, g.rho[h.n] * rsign * cphf, h.dm, acc);
+            hop_body<1>(W, q, h.lam * cphf, h.rho * rsign * cphf, h.dm, acc);
         }
         {
             const M3<float2> W = ll.load_smem(cur + LB, stride);
             float2 q[12];
             load_spinor(in + (size_t)cyb * 12, q);
-            hop_body<-1>(W, q, g.lam[h.n] * cphb, g.rho[h.n] * rsign * cphb, h.dm, acc);
+            hop_body<-1>(W, q, h.lam * cphb, h.rho * rsign * cphb, h.dm, acc);
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -588,9 +569,9 @@ __global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, 
     }
     const float rsign = mode == 1 ? -1.f : 1.f;
 #pragma unroll 1
-    for (int j = 0; j < NCANON; j++) {
-        const HopConst h = c_hop[j];
-        if (g.lam[h.n] == 0.f && g.rho[h.n] == 0.f) continue;  // class not in the operator
+    for (int t = 0; t < g.nhop; t++) {
+        const HopArg h = g.hop[t];
+        const int j = h.j;
         int yf, yb;
         float phf, phb;
         hop_nb(h.dm, site, nb, yf, phf, yb, phb);
@@ -598,13 +579,13 @@ __global__ void __launch_bounds__(TILE_THREADS) k_dslash_tiled(int mode, LL ll, 
             M3<float2> W = ll.load(j, site);
             float2 q[12];
             lds_spinor(sbase + (uint32_t)((hc + h.hd) * SSTR * 16), q);
-            hop_body<1>(W, q, g.lam[h.n] * phf, g.rho[h.n] * rsign * phf, h.dm, acc);
+            hop_body<1>(W, q, h.lam * phf, h.rho * rsign * phf, h.dm, acc);
         }
         {
             M3<float2> W = ll.load(j, yb);
             float2 q[12];
             lds_spinor(sbase + (uint32_t)((hc - h.hd) * SSTR * 16), q);
-            hop_body<-1>(W, q, g.lam[h.n] * phb, g.rho[h.n] * rsign * phb, h.dm, acc);
+            hop_body<-1>(W, q, h.lam * phb, h.rho * rsign * phb, h.dm, acc);
         }
     }
     float2 p[12];

@@ -148,9 +148,9 @@ __global__ void k_dslash_pair(int mode, PL pl, const float2 *__restrict__ in, fl
     for (int k = 0; k < 12; k++) acc.r[k] = acc.i[k] = make_float2(0.f, 0.f);
     const float rsign = mode == 1 ? -1.f : 1.f;
 #pragma unroll 1
-    for (int j = 0; j < NCANON; j++) {
-        const HopConst hc = c_hop[j];
-        if (g.lam[hc.n] == 0.f && g.rho[hc.n] == 0.f) continue;  // class not in the operator
+    for (int t = 0; t < g.nhop; t++) {
+        const HopArg hc = g.hop[t];
+        const int j = hc.j;
         int yfa, yba, yfb, ybb;
         float pfa, pba, pfb, pbb;
         hop_nb(hc.dm, sa, na, yfa, pfa, yba, pba);
@@ -158,8 +158,8 @@ __global__ void k_dslash_pair(int mode, PL pl, const float2 *__restrict__ in, fl
         float2 R[9], I[9];
         // forward hop: fields of the pair itself
         pair_load(pl, j, i, R, I);
-        pair_hop<1>(R, I, in + (size_t)yfa * 12, in + (size_t)yfb * 12, make_float2(g.lam[hc.n] * pfa, g.lam[hc.n] * pfb),
-                    make_float2(g.rho[hc.n] * rsign * pfa, g.rho[hc.n] * rsign * pfb), hc.dm, acc);
+        pair_hop<1>(R, I, in + (size_t)yfa * 12, in + (size_t)yfb * 12, make_float2(hc.lam * pfa, hc.lam * pfb),
+                    make_float2(hc.rho * rsign * pfa, hc.rho * rsign * pfb), hc.dm, acc);
         // reversed hop: fields at z = site - d for both sites
         const bool upper = yba >= H;
         pair_load(pl, j, upper ? ybb : yba, R, I);
@@ -167,8 +167,8 @@ __global__ void k_dslash_pair(int mode, PL pl, const float2 *__restrict__ in, fl
 #pragma unroll
             for (int e = 0; e < 9; e++) { R[e] = pswap(R[e]); I[e] = pswap(I[e]); }
         }
-        pair_hop<-1>(R, I, in + (size_t)yba * 12, in + (size_t)ybb * 12, make_float2(g.lam[hc.n] * pba, g.lam[hc.n] * pbb),
-                     make_float2(g.rho[hc.n] * rsign * pba, g.rho[hc.n] * rsign * pbb), hc.dm, acc);
+        pair_hop<-1>(R, I, in + (size_t)yba * 12, in + (size_t)ybb * 12, make_float2(hc.lam * pba, hc.lam * pbb),
+                     make_float2(hc.rho * rsign * pba, hc.rho * rsign * pbb), hc.dm, acc);
     }
     const float dg = (float)diag;
     float2 pa[12], pb[12], oa[12], ob[12];

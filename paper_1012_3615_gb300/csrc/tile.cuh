@@ -1,9 +1,8 @@
-// Tile shape of the shared-memory stencil kernel (sites per CTA along x, y, z, t).
+// Which lattices the shared-memory stencil kernel takes (tile shape TX..TT in common.cuh).
 #pragma once
 #include "common.cuh"
 
 namespace bri {
-constexpr int TX = 8, TY = 4, TZ = 2, TT = 2;
 // the tiled kernel needs every extent to be a multiple of the tile
 BRI_HD bool tiled_ok(const Geom &g) {
     return g.L[0] % TX == 0 && g.L[1] % TY == 0 && g.L[2] % TZ == 0 && g.L[3] % TT == 0;
