@@ -209,6 +209,75 @@ bri_status bri_cdot(bri_ctx *ctx, double *result, const void *a, const void *b, 
 bri_status bri_set_weights(bri_ctx *ctx, const double *lambda, const double *rho);
 bri_status bri_get_weights(bri_ctx *ctx, double *lambda, double *rho);
 
+/* ---- spectra and the overlap operator (Sec. 7) ------------------------------ */
+
+typedef struct {
+    int nconv;        /* wanted Ritz pairs whose residual estimate met tol */
+    int krylov_dim;   /* Lanczos vectors built */
+    int applies;      /* stencil applications */
+    double max_resid; /* largest relative residual estimate |A y - theta y| / theta */
+    double seconds;
+    bri_status status;
+} bri_eig_info;
+
+/* Extremal eigenvalues of A = D(m0)^dagger D(m0) = (gamma5 D(m0))^2 -- the
+ * Ritz values of the Lanczos process on A that Sec. 7.4 compares between
+ * kernels (at m0 = -rho, A is the square of the shifted hermitian kernel).
+ * Lanczos with full reorthogonalisation; the basis (max_krylov + 1 FP64
+ * vectors of 12 V complex numbers) is allocated for the call and freed.
+ * evals: host, nev doubles, the nev smallest eigenvalues ascending; lmax: host
+ * double or NULL, the largest; evecs: device [nev][V][4][3] complex128 or NULL,
+ * the Ritz vectors (unit norm).  Converged when every residual estimate is
+ * below tol x its Ritz value.  Uses the FP64 hopping fields and the class
+ * weights set on ctx.  Synchronises the stream.  nev in [1, 64], max_krylov
+ * in [nev + 1, 12 V].  Errors: BRI_EINVAL, BRI_ESTATE (no FP64 fields),
+ * BRI_ENOTCONV (max_krylov reached; evals hold the last Ritz values),
+ * BRI_ENOMEM. */
+bri_status bri_eigs_ddag_d(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0,
+                           int max_krylov, double tol, bri_eig_info *info, void *stream);
+
+typedef struct {
+    int nlow;          /* deflated eigenpairs of H */
+    int degree;        /* degree of the Chebyshev polynomial p, p(x) ~ 1/sqrt(x) */
+    double lo, hi;     /* interval of H^2 (deflated) on which p is built */
+    double err_bound;  /* max over [lo, hi] of |1 - sqrt(x) p(x)| (dense grid) */
+    double defl_resid; /* largest ||H z - lambda z|| of the deflated pairs */
+    int krylov_dim;    /* Lanczos vectors built, both runs */
+    int applies;       /* stencil applications of the setup */
+    double seconds;
+    bri_status status;
+} bri_overlap_info;
+
+/* Prepare the overlap operator of Eq. def_over on the current operator D
+ * (links and class weights of ctx): H = gamma5 (D - rho),
+ *   sign(H) psi = sum_i sign(lambda_i) z_i <z_i, psi> + H p(P H^2 P) P psi,
+ * with (lambda_i, z_i) the nlow eigenpairs of H of smallest |lambda| (Lanczos
+ * on H^2 to relative residual tol, then Rayleigh-Ritz with H), P the projector
+ * orthogonal to them, and p the Chebyshev interpolant of 1/sqrt(x) on
+ * [lo, hi] (the rest of the spectrum of H^2, from a second Lanczos run on the
+ * deflated operator, widened by 2%) of the smallest degree whose sign error
+ * max |1 - sqrt(x) p(x)| is <= eps.  prec: arithmetic of the polynomial
+ * (BRI_F64, or BRI_F32 / BRI_F16 with the FP32 / FP16 hopping fields of that
+ * precision; deflation and the final sum stay FP64).  State is kept in ctx
+ * until the next setup; changing the links or weights invalidates it.
+ * Synchronises the stream.  rho in (0, 2), nlow in [0, 64], eps in
+ * [1e-14, 0.1].  Errors: BRI_EINVAL (also when the degree would exceed
+ * 60000), BRI_ESTATE, BRI_ENOTCONV, BRI_ENOMEM. */
+bri_status bri_overlap_setup(bri_ctx *ctx, double rho, int nlow, double eps, int max_krylov, double tol,
+                             bri_prec prec, bri_overlap_info *info, void *stream);
+
+/* The deflated eigenpairs of the last setup: lambda (host, nlow doubles,
+ * ascending |lambda|) and/or vecs (device [nlow][V][4][3] complex128); either
+ * may be NULL.  Errors: BRI_ESTATE (no valid setup). */
+bri_status bri_overlap_modes(bri_ctx *ctx, double *lambda, double *vecs, void *stream);
+
+/* out = sign(H) in (bri_apply_sign) or out = D_ov,m in with
+ * D_ov,m = (1 - m / (2 rho)) rho [1 + gamma5 sign(H)] + m (bri_apply_overlap,
+ * Eq. def_over and Eq. def_mass, lattice spacing 1).  in, out: device
+ * [nrhs][V][4][3] complex128, distinct.  Errors: BRI_EINVAL, BRI_ESTATE. */
+bri_status bri_apply_sign(bri_ctx *ctx, double *out, const double *in, int nrhs, void *stream);
+bri_status bri_apply_overlap(bri_ctx *ctx, double *out, const double *in, int nrhs, double m, void *stream);
+
 /* Tune the launch shape of the apply kernels for (prec, nrhs) on this
  * lattice (timed with CUDA events, result cached in the context and, when the
  * environment variable BRI_TUNE_CACHE names a file, in that file).

@@ -32,6 +32,27 @@ class bri_solve_info(ctypes.Structure):
                 "seconds": self.seconds, "status": STATUS_NAMES.get(self.status, self.status)}
 
 
+class bri_eig_info(ctypes.Structure):
+    _fields_ = [("nconv", c_int), ("krylov_dim", c_int), ("applies", c_int), ("max_resid", c_double),
+                ("seconds", c_double), ("status", c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status"] = STATUS_NAMES.get(self.status, self.status)
+        return d
+
+
+class bri_overlap_info(ctypes.Structure):
+    _fields_ = [("nlow", c_int), ("degree", c_int), ("lo", c_double), ("hi", c_double), ("err_bound", c_double),
+                ("defl_resid", c_double), ("krylov_dim", c_int), ("applies", c_int), ("seconds", c_double),
+                ("status", c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status"] = STATUS_NAMES.get(self.status, self.status)
+        return d
+
+
 # name -> (restype, argtypes), mirroring include/brillouin.h
 SIGNATURES = {
     "bri_create": (c_int, [ctypes.POINTER(bri_lattice), ctypes.POINTER(c_void_p)]),
@@ -51,6 +72,13 @@ SIGNATURES = {
     "bri_cdot": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "bri_set_weights": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "bri_get_weights": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "bri_eigs_ddag_d": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double), c_void_p, c_int,
+                                c_double, c_int, c_double, ctypes.POINTER(bri_eig_info), c_void_p]),
+    "bri_overlap_setup": (c_int, [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int,
+                                  ctypes.POINTER(bri_overlap_info), c_void_p]),
+    "bri_overlap_modes": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p]),
+    "bri_apply_sign": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "bri_apply_overlap": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "bri_tune": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "bri_set_threads": (c_int, [c_void_p, c_int, c_int, c_int]),
     "bri_get_threads": (c_int, [c_void_p, c_int, c_int]),

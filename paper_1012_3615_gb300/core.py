@@ -166,6 +166,47 @@ class Brillouin:
             x = z
         return lam
 
+    # ---- spectra and the overlap operator (Sec. 7) -----------------------------------
+    def eigs_ddag_d(self, nev, m0=0.0, max_krylov=500, tol=1e-10, vectors=False):
+        """nev smallest and the largest eigenvalue of D(m0)^dagger D(m0) (Lanczos
+        in the library).  Returns (evals, lmax, info) or (evals, lmax, vecs, info)."""
+        ev = (ctypes.c_double * nev)()
+        lmax = ctypes.c_double()
+        info = abi.bri_eig_info()
+        vecs = torch.empty((nev, self.V, 4, 3), dtype=torch.complex128, device="cuda") if vectors else None
+        st = self.lib.bri_eigs_ddag_d(self.ctx, ev, ctypes.byref(lmax), _ptr(vecs) if vectors else None, int(nev),
+                                      float(m0), int(max_krylov), float(tol), ctypes.byref(info), _stream())
+        if st not in (0, abi.BRI_ENOTCONV):
+            self._check(st)
+        out = (list(ev), lmax.value) + ((vecs,) if vectors else ()) + (info.as_dict(),)
+        return out
+
+    def overlap_setup(self, rho=1.0, nlow=0, eps=1e-10, max_krylov=500, tol=1e-10, prec="f64"):
+        """Prepare sign(H), H = gamma5 (D - rho) (Eq. def_over); returns the setup info."""
+        info = abi.bri_overlap_info()
+        self._check(self.lib.bri_overlap_setup(self.ctx, float(rho), int(nlow), float(eps), int(max_krylov),
+                                               float(tol), _PREC[prec], ctypes.byref(info), _stream()))
+        return info.as_dict()
+
+    def overlap_modes(self, nlow):
+        lam = (ctypes.c_double * max(nlow, 1))()
+        vecs = torch.empty((max(nlow, 1), self.V, 4, 3), dtype=torch.complex128, device="cuda")
+        self._check(self.lib.bri_overlap_modes(self.ctx, lam, _ptr(vecs), _stream()))
+        return list(lam)[:nlow], vecs[:nlow]
+
+    def sign(self, psi, out=None):
+        n = self._spinor(psi, "f64")
+        out = torch.empty_like(psi) if out is None else out
+        self._check(self.lib.bri_apply_sign(self.ctx, _ptr(out), _ptr(psi), n, _stream()))
+        return out
+
+    def overlap(self, psi, m=0.0, out=None):
+        """D_ov,m psi (Eq. def_over, Eq. def_mass) after overlap_setup."""
+        n = self._spinor(psi, "f64")
+        out = torch.empty_like(psi) if out is None else out
+        self._check(self.lib.bri_apply_overlap(self.ctx, _ptr(out), _ptr(psi), n, float(m), _stream()))
+        return out
+
     # ---- weights of the rho/lambda class (Sec. 8, Tab. rholambda) -------------
     def set_weights(self, lam, rho):
         """lam: lambda_0..4, rho: rho_0..4 (rho_0 ignored)."""

@@ -97,6 +97,7 @@ bri_status bri_create(const bri_lattice *lat, bri_ctx **out) {
 bri_status bri_destroy(bri_ctx *ctx) {
     if (!ctx) return BRI_OK;
     bri_solver_free(ctx);
+    bri_overlap_free(ctx);
     cudaFree(ctx->U);
     cudaFree(ctx->hops64);
     for (LinkStore *st : {&ctx->f32, &ctx->f16, &ctx->p32, &ctx->p16}) {
@@ -117,6 +118,7 @@ bri_status bri_build_hops(bri_ctx *ctx, const double *U, bri_prec prec, bri_comp
     const size_t bytes = sizeof(double2) * 36 * (size_t)ctx->g.V;
     if (!ctx->U) BRI_TRY_CUDA(ctx, cudaMalloc(&ctx->U, bytes));
     BRI_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->U, U, bytes, cudaMemcpyDeviceToDevice, s));
+    ctx->gen++;
     BRI_RETURN_IF(bri_hops_build_impl(ctx, s));
     return bri_hops_store_impl(ctx, prec, comp, s);
 }
@@ -127,6 +129,7 @@ bri_status bri_store_hops(bri_ctx *ctx, bri_prec prec, bri_comp comp, void *stre
     if (comp != BRI_LINK_FULL && comp != BRI_LINK_2ROW && comp != BRI_LINK_8PARAM)
         return bri_fail(ctx, BRI_EINVAL, "invalid compression");
     if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    ctx->gen++;
     return bri_hops_store_impl(ctx, prec, comp, as_stream(stream));
 }
 
@@ -251,7 +254,57 @@ bri_status bri_set_weights(bri_ctx *ctx, const double *lambda, const double *rho
         if (!std::isfinite(lambda[n]) || (n > 0 && !std::isfinite(rho[n])))
             return bri_fail(ctx, BRI_EINVAL, "weights must be finite");
     geom_set_weights(ctx->g, lambda, rho);
+    ctx->gen++;
     return BRI_OK;
+}
+
+// ---- spectra and the overlap operator ------------------------------------------------
+bri_status bri_eigs_ddag_d(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0,
+                           int max_krylov, double tol, bri_eig_info *info, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!evals) return bri_fail(ctx, BRI_EINVAL, "evals must be a host array of nev doubles");
+    if (evecs && !bri_aligned16(evecs)) return bri_fail(ctx, BRI_EINVAL, "evecs must be 16-byte aligned");
+    if (nev < 1 || nev > 64) return bri_fail(ctx, BRI_EINVAL, "nev must be in [1, 64]");
+    if (max_krylov <= nev || (size_t)max_krylov > 12 * (size_t)ctx->g.V)
+        return bri_fail(ctx, BRI_EINVAL, "max_krylov must be in [nev + 1, 12 V]");
+    if (!(tol > 0) || !std::isfinite(m0)) return bri_fail(ctx, BRI_EINVAL, "tol must be > 0 and m0 finite");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    return bri_eigs_impl(ctx, evals, lmax, evecs, nev, m0, max_krylov, tol, info, as_stream(stream));
+}
+
+bri_status bri_overlap_setup(bri_ctx *ctx, double rho, int nlow, double eps, int max_krylov, double tol,
+                             bri_prec prec, bri_overlap_info *info, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!(rho > 0 && rho < 2)) return bri_fail(ctx, BRI_EINVAL, "rho must be in (0, 2)");
+    if (nlow < 0 || nlow > 64) return bri_fail(ctx, BRI_EINVAL, "nlow must be in [0, 64]");
+    if (!(eps >= 1e-14 && eps <= 0.1)) return bri_fail(ctx, BRI_EINVAL, "eps must be in [1e-14, 0.1]");
+    if (max_krylov <= nlow + 1 || (size_t)max_krylov > 12 * (size_t)ctx->g.V)
+        return bri_fail(ctx, BRI_EINVAL, "max_krylov must be in [nlow + 2, 12 V]");
+    if (!(tol > 0)) return bri_fail(ctx, BRI_EINVAL, "tol must be > 0");
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    if ((prec == BRI_F32 && !ctx->f32.valid) || (prec == BRI_F16 && !ctx->f16.valid))
+        return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
+    return bri_overlap_setup_impl(ctx, rho, nlow, eps, max_krylov, tol, prec, info, as_stream(stream));
+}
+
+bri_status bri_overlap_modes(bri_ctx *ctx, double *lambda, double *vecs, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (vecs && !bri_aligned16(vecs)) return bri_fail(ctx, BRI_EINVAL, "vecs must be 16-byte aligned");
+    return bri_overlap_modes_impl(ctx, lambda, vecs, as_stream(stream));
+}
+
+bri_status bri_apply_sign(bri_ctx *ctx, double *out, const double *in, int nrhs, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, BRI_F64));
+    return bri_overlap_apply_impl(ctx, out, in, nrhs, 0, 0.0, as_stream(stream));
+}
+
+bri_status bri_apply_overlap(bri_ctx *ctx, double *out, const double *in, int nrhs, double m, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, BRI_F64));
+    if (!std::isfinite(m)) return bri_fail(ctx, BRI_EINVAL, "m must be finite");
+    return bri_overlap_apply_impl(ctx, out, in, nrhs, 1, m, as_stream(stream));
 }
 
 bri_status bri_get_weights(bri_ctx *ctx, double *lambda, double *rho) {

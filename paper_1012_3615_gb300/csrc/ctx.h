@@ -16,7 +16,8 @@ struct LinkStore {
     void *b = nullptr;  // tail array (8/4-byte chunk, [40][V]) or null
 };
 
-struct SolverWork;  // solver work spaces (solve.cu)
+struct SolverWork;   // solver work spaces (solve.cu)
+struct OverlapWork;  // Lanczos / overlap state (overlap.cu)
 
 struct bri_ctx {
     bri::Geom g;
@@ -27,6 +28,8 @@ struct bri_ctx {
     LinkStore f32, f16;
     LinkStore p32, p16;  // site-pair interleaved copies (full / 2-row, even t extent)
     SolverWork *work = nullptr;
+    OverlapWork *ov = nullptr;
+    long gen = 0;  // bumped whenever the operator changes (links, weights)
     std::map<std::string, int> tune;  // launch-shape cache: key -> threads per block
     std::string err;
     long launches = 0;
@@ -78,5 +81,14 @@ bri_status bri_cdot_impl(bri_ctx *ctx, double *res, const void *a, const void *b
                          cudaStream_t user);
 bri_status bri_dp_levels(bri_ctx *ctx, void *A, const int *klist, const int start[6], cudaStream_t s);
 bri_status bri_force_impl(bri_ctx *ctx, double2 *dU, const double2 *chi, const double2 *psi, cudaStream_t s);
+void bri_overlap_free(bri_ctx *ctx);
+bri_status bri_eigs_impl(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0, int max_krylov,
+                         double tol, bri_eig_info *info, cudaStream_t s);
+bri_status bri_overlap_setup_impl(bri_ctx *ctx, double rho, int nlow, double eps, int max_krylov, double tol,
+                                  bri_prec prec, bri_overlap_info *info, cudaStream_t s);
+bri_status bri_overlap_modes_impl(bri_ctx *ctx, double *lambda, double *vecs, cudaStream_t s);
+// mode 0: out = sign(H) in; mode 1: out = D_ov,m in
+bri_status bri_overlap_apply_impl(bri_ctx *ctx, double *out, const double *in, int nrhs, int mode, double m,
+                                  cudaStream_t s);
 bri_status bri_solve_impl(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol, int maxit,
                           int mode, bri_solve_info *info, cudaStream_t user);
