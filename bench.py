@@ -380,6 +380,9 @@ def native(args, world, rank, local, pg):
     if args.rows:
         torch.cuda.empty_cache()
         line["rows"] = rows_bench(dev)
+    if args.study:
+        torch.cuda.empty_cache()
+        line["study"] = study_bench(dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -505,6 +508,88 @@ def solve_bench(args, dev):
     return out
 
 
+def study_bench(dev):
+    """Comparisons between members of the operator class on one synthetic field
+    (12^4, links exp(i0.3H), antiperiodic t), Wilson against Brillouin:
+    A (Sec. 7.4): smallest, 10th and largest eigenvalue of D^dagger D at
+      m0 = -1 (the shifted overlap kernel, rho = 1), the condition numbers with
+      and without the 9 lowest modes, and the sign-function polynomial degree
+      for eps = 1e-10 after deflating 9 modes (FP32 polynomial), with the time
+      of one overlap application.
+    B (Sec. 6.4, Sec. 8): BiCGstab (FP64, true residual 1e-10, Z2 source) for
+      each operator at its own "critical" bare mass -- where the smallest
+      eigenvalue of D^dagger D is smallest on this volume -- and 0.1 above it:
+      iterations and time."""
+    import torch
+
+    from paper_1012_3615_gb300 import Brillouin, synth
+    from paper_1012_3615_gb300.core import WEIGHTS
+
+    L = (12, 12, 12, 12)
+    U = synth.random_su3_links_torch(L, 0.3, SEED + 11, device=dev)
+    b = torch.as_tensor(synth.z2_spinor(L, 1, SEED + 12), device=dev)
+    psi = synth.gaussian_spinor_torch(L, 1, SEED + 13, device=dev)
+    out = {"lattice": list(L), "links": "exp(i0.3H)"}
+    for name in ("wilson", "brillouin"):
+        op = Brillouin(L, BC)
+        op.set_weights(*WEIGHTS[name])
+        op.build_hops(U, prec="f32", comp="full")
+        r = {}
+        ev, lmax, info = op.eigs_ddag_d(10, m0=-1.0, max_krylov=3000, tol=1e-8)
+        r["ritz_m0_-1"] = {"lambda_1": ev[0], "lambda_10": ev[9], "lambda_max": lmax,
+                           "cond": lmax / ev[0], "cond_without_9": lmax / ev[9],
+                           "krylov_dim": info["krylov_dim"], "status": info["status"]}
+        ov = op.overlap_setup(rho=1.0, nlow=9, eps=1e-10, max_krylov=3000, tol=1e-10, prec="f32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op.overlap(psi)
+        torch.cuda.synchronize()
+        r["overlap_rho_1_nlow_9"] = dict(ov, apply_seconds=time.perf_counter() - t0)
+
+        def lmin(m0):
+            e, _, _ = op.eigs_ddag_d(1, m0=m0, max_krylov=2000, tol=1e-2)
+            return e[0]
+
+        # the bare mass where the smallest eigenvalue of D^dagger D is smallest
+        # (on a finite volume it stays above the lowest-momentum gap): golden
+        # section over [-0.6, 0.3]; then solve there and 0.1 above it
+        g = (5 ** 0.5 - 1) / 2
+        a_, b_ = -0.6, 0.3
+        c_, d_ = b_ - g * (b_ - a_), a_ + g * (b_ - a_)
+        fc_, fd_ = lmin(c_), lmin(d_)
+        for _ in range(14):
+            if fc_ < fd_:
+                b_, d_, fd_ = d_, c_, fc_
+                c_ = b_ - g * (b_ - a_)
+                fc_ = lmin(c_)
+            else:
+                a_, c_, fc_ = c_, d_, fd_
+                d_ = a_ + g * (b_ - a_)
+                fd_ = lmin(d_)
+        mstar = 0.5 * (a_ + b_)
+        for tag, m0 in (("solve_at_gap_minimum", mstar), ("solve_0.1_above", mstar + 0.1)):
+            lm = lmin(m0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, inf = op.solve(b, m0=m0, tol=1e-10, maxit=20000, mode=0)
+            torch.cuda.synchronize()
+            r[tag] = {"m0": m0, "lambda_min": lm, "iters": inf[0]["iters"], "applies": 2 * inf[0]["iters"],
+                      "status": inf[0]["status"], "true_resid": inf[0]["true_resid"],
+                      "seconds": time.perf_counter() - t0}
+        out[name] = r
+        del op
+        torch.cuda.empty_cache()
+    w, br = out["wilson"], out["brillouin"]
+    out["brillouin_over_wilson"] = {
+        "iterations_at_gap_minimum": br["solve_at_gap_minimum"]["iters"] / w["solve_at_gap_minimum"]["iters"],
+        "iterations_0.1_above": br["solve_0.1_above"]["iters"] / w["solve_0.1_above"]["iters"],
+        "solve_time_at_gap_minimum": br["solve_at_gap_minimum"]["seconds"] / w["solve_at_gap_minimum"]["seconds"],
+        "lambda_max_m0_-1": br["ritz_m0_-1"]["lambda_max"] / w["ritz_m0_-1"]["lambda_max"],
+        "cond_without_9": br["ritz_m0_-1"]["cond_without_9"] / w["ritz_m0_-1"]["cond_without_9"],
+        "sign_degree": br["overlap_rho_1_nlow_9"]["degree"] / w["overlap_rho_1_nlow_9"]["degree"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,6 +602,8 @@ def main():
     ap.add_argument("--solve", action="store_true", help="add the solver workloads (time to 1e-10)")
     ap.add_argument("--solve-small", action="store_true", help="only the 16^3x32 solver workload")
     ap.add_argument("--rows", action="store_true", help="add hop precompute, FP64 apply and force timings")
+    ap.add_argument("--study", action="store_true",
+                    help="add the Wilson / Brillouin comparison (Sec. 7.4 spectra, overlap degree, solver iterations)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lattice", type=lambda t: [int(v) for v in t.split(",")], default=None,

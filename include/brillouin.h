@@ -254,8 +254,10 @@ typedef struct {
  * with (lambda_i, z_i) the nlow eigenpairs of H of smallest |lambda| (Lanczos
  * on H^2 to relative residual tol, then Rayleigh-Ritz with H), P the projector
  * orthogonal to them, and p the Chebyshev interpolant of 1/sqrt(x) on
- * [lo, hi] (the rest of the spectrum of H^2, from a second Lanczos run on the
- * deflated operator, widened by 2%) of the smallest degree whose sign error
+ * [lo, hi] (the rest of the spectrum of H^2: the extreme Ritz values, minus /
+ * plus their residuals, of a second Lanczos run on the deflated operator to
+ * relative residual max(tol, 1e-4), widened by 2%) of the smallest degree
+ * whose sign error
  * max |1 - sqrt(x) p(x)| is <= eps.  prec: arithmetic of the polynomial
  * (BRI_F64, or BRI_F32 / BRI_F16 with the FP32 / FP16 hopping fields of that
  * precision; deflation and the final sum stay FP64).  State is kept in ctx
