@@ -221,3 +221,34 @@ def apply_sites(L, bc, U, m0, psi, sites):
         lib().bo_apply_site(_iv(L), _iv(bc), _p(U), ctypes.c_double(m0), ctypes.c_long(int(s)), _p(psi), _p(o))
         out[i] = o
     return out
+
+
+def ape_smear(L, U, alpha, nsteps=1):
+    """nsteps APE steps (Eq. def_ape, projection of Eq. proj_SU) of the links U."""
+    V = int(np.prod(L))
+    U = _c(U, (V, 4, 3, 3))
+    out = np.zeros_like(U)
+    if lib().bo_ape_smear(_iv(L), _p(U), ctypes.c_double(alpha), int(nsteps), _p(out)) != 0:
+        raise MemoryError("ape_smear")
+    return out
+
+
+def clover_field(L, U):
+    """Hermitian clover-leaf F_{mu nu}(x), (V, 6, 3, 3), planes 01, 02, 03, 12, 13, 23."""
+    V = int(np.prod(L))
+    U = _c(U, (V, 4, 3, 3))
+    F = np.zeros((V, 6, 3, 3), np.complex128)
+    lib().bo_clover_field(_iv(L), _p(U), _p(F))
+    return F
+
+
+def apply_clover(L, bc, W, U, m0, csw, psi, dagger=False):
+    """D psi with the clover term -(c_SW/2) sum sigma F of Eq. def_pref, F built
+    from the links U (the same links the hops W were built from)."""
+    out = apply(L, bc, W, m0, psi, dagger=dagger)
+    V = int(np.prod(L))
+    psi = _c(psi, (V, 4, 3))
+    U = _c(U, (V, 4, 3, 3))
+    if lib().bo_clover_add(_iv(L), _p(U), ctypes.c_double(csw), _p(psi), _p(out)) != 0:
+        raise MemoryError("apply_clover")
+    return out

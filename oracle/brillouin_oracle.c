@@ -827,3 +827,161 @@ int bo_apply_site(const int L[4], const int bc[4], const cplx *U, double m0, lon
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* APE smearing (Eq. def_ape) and the clover term of Eq. def_pref       */
+/* ------------------------------------------------------------------ */
+/* U_{s mu}(x): the link leaving x in direction s*mu (s = +1 or -1),
+ * U_{-mu}(x) = U_mu(x - mu)^dagger */
+static void dir_link(const int L[4], const cplx *U, const int x[4], int mu, int s, cplx out[9]) {
+    if (s > 0) {
+        memcpy(out, U + (index_of(L, x) * 4 + mu) * 9, 9 * sizeof(cplx));
+    } else {
+        int d[4] = {0, 0, 0, 0};
+        d[mu] = -1;
+        long y = shifted(L, NULL, x, d, NULL);
+        m3_dag(U + (y * 4 + mu) * 9, out);
+    }
+}
+
+/* one APE step, written as printed: for every link
+ *   V_mu(x) = P_SU(3){ (1 - alpha) 1 + alpha/6 sum_{+-nu != mu}
+ *             U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger U_mu(x)^dagger } U_mu(x)
+ * where for nu negative every U_nu is the link in direction -nu. */
+int bo_ape_step(const int L[4], const cplx *U, double alpha, cplx *Vout) {
+    long V = volume(L);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < V; s++) {
+        int x[4];
+        coords(L, s, x);
+        for (int mu = 0; mu < 4; mu++) {
+            const cplx *Umu = U + (s * 4 + mu) * 9;
+            cplx Umu_dag[9], S[9];
+            m3_dag(Umu, Umu_dag);
+            for (int i = 0; i < 9; i++) S[i] = 0;
+            for (int nu = 0; nu < 4; nu++) {
+                if (nu == mu) continue;
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int dn[4] = {0, 0, 0, 0}, dm[4] = {0, 0, 0, 0};
+                    dn[nu] = sg;
+                    dm[mu] = 1;
+                    int xn[4], xm[4];
+                    coords(L, shifted(L, NULL, x, dn, NULL), xn);
+                    coords(L, shifted(L, NULL, x, dm, NULL), xm);
+                    cplx a[9], b[9], c[9], t[9];
+                    dir_link(L, U, x, nu, sg, a);                           /* U_nu(x) */
+                    memcpy(b, U + (index_of(L, xn) * 4 + mu) * 9, sizeof b); /* U_mu(x + nu) */
+                    dir_link(L, U, xm, nu, sg, c);                          /* U_nu(x + mu) */
+                    m3_dag(c, c);
+                    m3_mul(a, b, t);
+                    m3_mul(t, c, t);
+                    m3_mul(t, Umu_dag, t);
+                    for (int i = 0; i < 9; i++) S[i] += t[i];
+                }
+            }
+            cplx X[9], Y[9];
+            m3_eye(X);
+            for (int i = 0; i < 9; i++) X[i] = (1.0 - alpha) * X[i] + alpha / 6.0 * S[i];
+            bo_project_su3(X, Y);
+            m3_mul(Y, Umu, Vout + (s * 4 + mu) * 9);
+        }
+    }
+    return 0;
+}
+
+int bo_ape_smear(const int L[4], const cplx *U, double alpha, int nsteps, cplx *Vout) {
+    long n = volume(L) * 36;
+    cplx *a = malloc(n * sizeof(cplx));
+    if (!a) return -1;
+    memcpy(Vout, U, n * sizeof(cplx));
+    for (int k = 0; k < nsteps; k++) {
+        bo_ape_step(L, Vout, alpha, a);
+        memcpy(Vout, a, n * sizeof(cplx));
+    }
+    free(a);
+    return 0;
+}
+
+/* plaquette leaf U_{s mu}(x) U_{t nu}(x + s mu) U_{s mu}(x + t nu)^dagger U_{t nu}(x)^dagger */
+static void leaf(const int L[4], const cplx *U, const int x[4], int mu, int s, int nu, int t, cplx out[9]) {
+    int dmu[4] = {0, 0, 0, 0}, dnu[4] = {0, 0, 0, 0};
+    dmu[mu] = s;
+    dnu[nu] = t;
+    int xm[4], xn[4];
+    coords(L, shifted(L, NULL, x, dmu, NULL), xm);
+    coords(L, shifted(L, NULL, x, dnu, NULL), xn);
+    cplx a[9], b[9], c[9], d[9];
+    dir_link(L, U, x, mu, s, a);
+    dir_link(L, U, xm, nu, t, b);
+    dir_link(L, U, xn, mu, s, c);
+    dir_link(L, U, x, nu, t, d);
+    m3_dag(c, c);
+    m3_dag(d, d);
+    m3_mul(a, b, out);
+    m3_mul(out, c, out);
+    m3_mul(out, d, out);
+}
+
+/* hermitian clover-leaf field strength F_{mu nu}(x) = (Q - Q^dagger) / (8 i),
+ * Q = sum of the four leaves of the (mu, nu) plane at x, all with the same
+ * orientation (mu then nu; nu then -mu; -mu then -nu; -nu then mu).
+ * F: [V][6][3][3] for the planes (01, 02, 03, 12, 13, 23). */
+int bo_clover_field(const int L[4], const cplx *U, cplx *F) {
+    long V = volume(L);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < V; s++) {
+        int x[4];
+        coords(L, s, x);
+        int p = 0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++, p++) {
+                cplx Q[9], t[9];
+                for (int i = 0; i < 9; i++) Q[i] = 0;
+                leaf(L, U, x, mu, +1, nu, +1, t);
+                for (int i = 0; i < 9; i++) Q[i] += t[i];
+                leaf(L, U, x, nu, +1, mu, -1, t);
+                for (int i = 0; i < 9; i++) Q[i] += t[i];
+                leaf(L, U, x, mu, -1, nu, -1, t);
+                for (int i = 0; i < 9; i++) Q[i] += t[i];
+                leaf(L, U, x, nu, -1, mu, +1, t);
+                for (int i = 0; i < 9; i++) Q[i] += t[i];
+                cplx *f = F + (s * 6 + p) * 9;
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) f[3 * i + j] = (Q[3 * i + j] - conj(Q[3 * j + i])) / (8.0 * _Complex_I);
+            }
+    }
+    return 0;
+}
+
+/* out += -(c_SW / 2) sum_{mu < nu} sigma_{mu nu} (x) F_{mu nu}(x) in(x),
+ * sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu]; F from the links U */
+int bo_clover_add(const int L[4], const cplx *U, double csw, const cplx *in, cplx *out) {
+    long V = volume(L);
+    cplx *F = malloc(V * 54 * sizeof(cplx));
+    if (!F) return -1;
+    bo_clover_field(L, U, F);
+    cplx g[4][16], sig[6][16];
+    for (int mu = 0; mu < 4; mu++) bo_gamma(mu, g[mu]);
+    int p = 0;
+    for (int mu = 0; mu < 4; mu++)
+        for (int nu = mu + 1; nu < 4; nu++, p++)
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++) {
+                    cplx c = 0;
+                    for (int k = 0; k < 4; k++) c += g[mu][4 * a + k] * g[nu][4 * k + b] - g[nu][4 * a + k] * g[mu][4 * k + b];
+                    sig[p][4 * a + b] = 0.5 * _Complex_I * c;
+                }
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < V; s++)
+        for (int a = 0; a < 4; a++)
+            for (int c = 0; c < 3; c++) {
+                cplx sum = 0;
+                for (int q = 0; q < 6; q++)
+                    for (int b = 0; b < 4; b++)
+                        for (int cc = 0; cc < 3; cc++)
+                            sum += sig[q][4 * a + b] * F[(s * 6 + q) * 9 + 3 * c + cc] * in[s * 12 + 3 * b + cc];
+                out[s * 12 + 3 * a + c] += -0.5 * csw * sum;
+            }
+    free(F);
+    return 0;
+}
