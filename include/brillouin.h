@@ -209,6 +209,33 @@ bri_status bri_cdot(bri_ctx *ctx, double *result, const void *a, const void *b, 
 bri_status bri_set_weights(bri_ctx *ctx, const double *lambda, const double *rho);
 bri_status bri_get_weights(bri_ctx *ctx, double *lambda, double *rho);
 
+/* ---- link smearing and the clover term (Eq. def_ape, Eq. def_pref) --------- */
+
+/* nsteps steps of APE smearing (Eq. def_ape):
+ *   V_mu(x) = P_SU(3){ (1 - alpha) 1 + alpha/6 sum_{+-nu != mu}
+ *             U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger U_mu(x)^dagger } U_mu(x)
+ * (the paper uses alpha = 0.72 and 1 or 5 steps), P the projection of
+ * Eq. proj_SU, FP64.  Feeding V to bri_build_hops gives the fat-link operator
+ * of Sec. 5 (every thin link replaced, the clover term included).  U, V:
+ * device [V][4][3][3] complex128, distinct buffers; nsteps = 0 copies.
+ * Steps beyond the first use a temporary of the size of U (allocated and freed
+ * inside the call, which then synchronises the stream).  alpha in [0, 1],
+ * nsteps in [0, 1000].  Errors: BRI_EINVAL, BRI_ENOMEM. */
+bri_status bri_ape_smear(bri_ctx *ctx, double *V, const double *U, double alpha, int nsteps, void *stream);
+
+/* Switch on (csw != 0) or off (csw = 0) the clover term of Eq. def_pref,
+ *   -(c_SW/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x) delta_{x,y},
+ * sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F_{mu nu} = (Q - Q^dagger)/(8 i)
+ * the hermitian clover-leaf field strength (Q: the four plaquettes of the
+ * (mu, nu) plane around x, all oriented mu -> nu), from the links of the last
+ * bri_build_hops (rebuilt by every later bri_build_hops).  The paper takes the
+ * tree-level value c_SW = 1 (Sec. 5.3).  Every later apply (D, D^dagger, the
+ * overlap kernel, all precisions), solve and overlap setup includes the term;
+ * the force calls return BRI_ESTATE while it is on.  Stored per site as two
+ * hermitian 6x6 chiral blocks (576 B FP64 + 288 B FP32).  Errors: BRI_EINVAL,
+ * BRI_ESTATE (no links), BRI_ENOMEM. */
+bri_status bri_set_clover(bri_ctx *ctx, double csw, void *stream);
+
 /* ---- spectra and the overlap operator (Sec. 7) ------------------------------ */
 
 typedef struct {

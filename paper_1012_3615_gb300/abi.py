@@ -72,6 +72,8 @@ SIGNATURES = {
     "bri_cdot": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "bri_set_weights": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "bri_get_weights": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "bri_ape_smear": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]),
+    "bri_set_clover": (c_int, [c_void_p, c_double, c_void_p]),
     "bri_eigs_ddag_d": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double), c_void_p, c_int,
                                 c_double, c_int, c_double, ctypes.POINTER(bri_eig_info), c_void_p]),
     "bri_overlap_setup": (c_int, [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int,

@@ -166,6 +166,19 @@ class Brillouin:
             x = z
         return lam
 
+    # ---- link smearing and the clover term (Eq. def_ape, Eq. def_pref) ---------------
+    def ape_smear(self, U, alpha=0.72, nsteps=1, out=None):
+        """nsteps APE steps of the links U (cuda complex128 (V, 4, 3, 3))."""
+        if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous() and U.numel() == self.V * 36):
+            raise ValueError("U must be a contiguous cuda complex128 tensor of V*36 elements")
+        out = torch.empty_like(U) if out is None else out
+        self._check(self.lib.bri_ape_smear(self.ctx, _ptr(out), _ptr(U), float(alpha), int(nsteps), _stream()))
+        return out
+
+    def set_clover(self, csw):
+        """Clover coefficient c_SW of Eq. def_pref (0 switches the term off)."""
+        self._check(self.lib.bri_set_clover(self.ctx, float(csw), _stream()))
+
     # ---- spectra and the overlap operator (Sec. 7) -----------------------------------
     def eigs_ddag_d(self, nev, m0=0.0, max_krylov=500, tol=1e-10, vectors=False):
         """nev smallest and the largest eigenvalue of D(m0)^dagger D(m0) (Lanczos

@@ -98,6 +98,8 @@ bri_status bri_destroy(bri_ctx *ctx) {
     if (!ctx) return BRI_OK;
     bri_solver_free(ctx);
     bri_overlap_free(ctx);
+    cudaFree(ctx->clov64);
+    cudaFree(ctx->clov32);
     cudaFree(ctx->U);
     cudaFree(ctx->hops64);
     for (LinkStore *st : {&ctx->f32, &ctx->f16, &ctx->p32, &ctx->p16}) {
@@ -120,6 +122,7 @@ bri_status bri_build_hops(bri_ctx *ctx, const double *U, bri_prec prec, bri_comp
     BRI_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->U, U, bytes, cudaMemcpyDeviceToDevice, s));
     ctx->gen++;
     BRI_RETURN_IF(bri_hops_build_impl(ctx, s));
+    if (ctx->csw != 0.0) BRI_RETURN_IF(bri_clover_build_impl(ctx, s));  // F from the new links
     return bri_hops_store_impl(ctx, prec, comp, s);
 }
 
@@ -189,6 +192,7 @@ bri_status bri_force(bri_ctx *ctx, double *dU, const double *chi, const double *
     if (!dU || !chi || !psi || !bri_aligned16(dU) || !bri_aligned16(chi) || !bri_aligned16(psi))
         return bri_fail(ctx, BRI_EINVAL, "dU, chi, psi must be 16-byte aligned device pointers");
     if (!ctx->U) return bri_fail(ctx, BRI_ESTATE, "no links: call bri_build_hops first");
+    if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "the force of the clover term is not built (csw must be 0)");
     return bri_force_impl(ctx, (double2 *)dU, (const double2 *)chi, (const double2 *)psi, as_stream(stream));
 }
 
@@ -198,6 +202,7 @@ bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double
     if (!dU || !phi || !bri_aligned16(dU) || !bri_aligned16(phi))
         return bri_fail(ctx, BRI_EINVAL, "dU and phi must be 16-byte aligned device pointers");
     if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "the force of the clover term is not built (csw must be 0)");
     cudaStream_t s = as_stream(stream);
     const size_t n = (size_t)ctx->g.V * 12, bytes = n * sizeof(double2);
     double2 *Z = nullptr, *X = nullptr, *Y = nullptr, *t = nullptr;
@@ -256,6 +261,33 @@ bri_status bri_set_weights(bri_ctx *ctx, const double *lambda, const double *rho
     geom_set_weights(ctx->g, lambda, rho);
     ctx->gen++;
     return BRI_OK;
+}
+
+// ---- APE smearing and the clover term -------------------------------------------------
+bri_status bri_ape_smear(bri_ctx *ctx, double *V, const double *U, double alpha, int nsteps, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!V || !U || !bri_aligned16(V) || !bri_aligned16(U))
+        return bri_fail(ctx, BRI_EINVAL, "V and U must be 16-byte aligned device pointers");
+    const size_t bytes = sizeof(double2) * 36 * (size_t)ctx->g.V;
+    if ((const char *)V < (const char *)U + bytes && (const char *)U < (const char *)V + bytes)
+        return bri_fail(ctx, BRI_EINVAL, "V and U overlap");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return bri_fail(ctx, BRI_EINVAL, "alpha must be in [0, 1]");
+    if (nsteps < 0 || nsteps > 1000) return bri_fail(ctx, BRI_EINVAL, "nsteps must be in [0, 1000]");
+    return bri_ape_impl(ctx, (double2 *)V, (const double2 *)U, alpha, nsteps, as_stream(stream));
+}
+
+bri_status bri_set_clover(bri_ctx *ctx, double csw, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!std::isfinite(csw)) return bri_fail(ctx, BRI_EINVAL, "csw must be finite");
+    ctx->gen++;
+    ctx->csw = csw;
+    if (csw == 0.0) {
+        ctx->g.clov64 = nullptr;
+        ctx->g.clov32 = nullptr;
+        return BRI_OK;
+    }
+    if (!ctx->U) return bri_fail(ctx, BRI_ESTATE, "no links: call bri_build_hops first");
+    return bri_clover_build_impl(ctx, as_stream(stream));
 }
 
 // ---- spectra and the overlap operator ------------------------------------------------

@@ -148,6 +148,13 @@ struct Geom {
     double lamd[5], rhod[5];
     int nhop;
     HopArg hop[NCANON];
+    // clover term -(c_SW/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu} (Eq. def_pref) as two
+    // hermitian 6x6 chiral blocks per site (spins 0-1 and 2-3 x colour), each
+    // packed as 18 complex slots: the 6 real diagonal entries in slots 0-2, then
+    // the 15 upper entries row by row; FP64 [36][V], FP32 [18][V] float4
+    // (two slots each).  Null when the term is off.
+    const double2 *clov64;
+    const float4 *clov32;
 };
 inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) {
     for (int n = 0; n < 5; n++) {

@@ -29,6 +29,9 @@ struct bri_ctx {
     LinkStore p32, p16;  // site-pair interleaved copies (full / 2-row, even t extent)
     SolverWork *work = nullptr;
     OverlapWork *ov = nullptr;
+    double csw = 0.0;              // clover coefficient (0: no clover term)
+    double2 *clov64 = nullptr;     // clover blocks, see Geom
+    float4 *clov32 = nullptr;
     long gen = 0;  // bumped whenever the operator changes (links, weights)
     std::map<std::string, int> tune;  // launch-shape cache: key -> threads per block
     std::string err;
@@ -82,6 +85,9 @@ bri_status bri_cdot_impl(bri_ctx *ctx, double *res, const void *a, const void *b
 bri_status bri_dp_levels(bri_ctx *ctx, void *A, const int *klist, const int start[6], cudaStream_t s);
 bri_status bri_force_impl(bri_ctx *ctx, double2 *dU, const double2 *chi, const double2 *psi, cudaStream_t s);
 void bri_overlap_free(bri_ctx *ctx);
+bri_status bri_ape_impl(bri_ctx *ctx, double2 *V, const double2 *U, double alpha, int nsteps, cudaStream_t s);
+// (re)build the clover blocks from ctx->U with ctx->csw and switch the term on
+bri_status bri_clover_build_impl(bri_ctx *ctx, cudaStream_t s);
 bri_status bri_eigs_impl(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0, int max_krylov,
                          double tol, bri_eig_info *info, cudaStream_t s);
 bri_status bri_overlap_setup_impl(bri_ctx *ctx, double rho, int nlow, double eps, int max_krylov, double tol,

@@ -48,7 +48,7 @@ bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, dou
         const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
         if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
         const LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
-        if ((threads >> 11) == 3 && ps.valid) {
+        if ((threads >> 11) == 3 && ps.valid && !g.clov64) {
             // site-pair kernel on the interleaved copy
             const int thr = (threads & 2047) ? (threads & 2047) : 64;
             const int H = g.V / 2;

@@ -438,7 +438,57 @@ BRI_D void all_hops(std::integer_sequence<int, Js...>, const LL &ll, const typen
     (hop_pair<Js>(ll, in, site, nb, rsign, g, acc), ...);
 }
 
-template <class LL, int VAR>
+// o += C(x) p with the packed clover blocks of Geom (hermitian 6x6 per chirality)
+template <typename T>
+BRI_D void clover_block(const T c[18], const T *p, T *o) {
+    using R = decltype(c[0].x);
+    R d[6] = {c[0].x, c[0].y, c[1].x, c[1].y, c[2].x, c[2].y};
+    T r[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        r[i].x = d[i] * p[i].x;
+        r[i].y = d[i] * p[i].y;
+    }
+    int k = 3;
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i + 1; j < 6; j++, k++) {
+            const T e = c[k];  // C_ij; C_ji = conj(C_ij)
+            r[i].x += e.x * p[j].x - e.y * p[j].y;
+            r[i].y += e.x * p[j].y + e.y * p[j].x;
+            r[j].x += e.x * p[i].x + e.y * p[i].y;
+            r[j].y += e.x * p[i].y - e.y * p[i].x;
+        }
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        o[i].x += r[i].x;
+        o[i].y += r[i].y;
+    }
+}
+template <typename T>
+BRI_D void clover_add(const Geom &g, int site, const T p[12], T o[12]) {
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        T c[18];
+        if constexpr (sizeof(T) == 16) {
+#pragma unroll
+            for (int e = 0; e < 18; e++) c[e] = g.clov64[(size_t)(18 * b + e) * g.V + site];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 9; e++) {
+                const float4 q = g.clov32[(size_t)(9 * b + e) * g.V + site];
+                c[2 * e] = make_float2(q.x, q.y);
+                c[2 * e + 1] = make_float2(q.z, q.w);
+            }
+        }
+        clover_block(c, p + 6 * b, o + 6 * b);
+    }
+}
+
+// CLOV: add the clover term of Geom in the epilogue (a separate instantiation,
+// so that the kernels without it keep their register budget)
+template <class LL, int VAR, bool CLOV = false>
 __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out, Geom g,
                          double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
@@ -483,8 +533,12 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
             v.x -= acc.ai[i].y;
             v.y += acc.ai[i].x;
         }
-        if (mode == 2 && i >= 6) { v.x = -v.x; v.y = -v.y; }
         o[i] = v;
+    }
+    if constexpr (CLOV) clover_add(g, site, p, o);
+    if (mode == 2) {
+#pragma unroll
+        for (int i = 6; i < 12; i++) { o[i].x = -o[i].x; o[i].y = -o[i].y; }
     }
     store_spinor(out + (size_t)site * 12, o);
 }
@@ -618,6 +672,20 @@ template <class LL>
 void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
                    const int *skip, int threads, cudaStream_t s) {
     using T = typename LL::T;
+    if (g.clov64) {  // clover term on: the plain kernel (link prefetch variant for FP32) with the term
+        constexpr int VC = sizeof(T) == 8 ? 1 : 0;
+        static int max_c = 0;
+        if (max_c == 0) {
+            cudaFuncAttributes attr;
+            max_c = cudaFuncGetAttributes(&attr, k_dslash<LL, VC, true>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
+        }
+        int t = threads & 2047;
+        if (t == 0) t = 128;
+        if (t > max_c) t = max_c & ~31;
+        const dim3 grid((unsigned)((g.V + t - 1) / t), (unsigned)nrhs);
+        k_dslash<LL, VC, true><<<grid, t, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        return;
+    }
     if constexpr (sizeof(T) == 8) {
         if ((threads & 2047) == 0 && (threads >> 11) == 0 && tiled_ok(g)) {
             static bool attr_set = false;
