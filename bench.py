@@ -313,16 +313,17 @@ def native(args, world, rank, local, pg):
     peak, peak_kind = load_peaks()
     dslash_gbs = bytes_step / (ms * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers (pinned), copies timed
+    # end to end through the public API with host buffers (pinned): bri_apply_host
+    # copies the input in, applies and copies the result out (copies overlapping
+    # the stencil slab by slab); every step synchronises
     xh = x.cpu().pin_memory()
     oh = torch.empty_like(xh).pin_memory()
     e2e_steps = max(2, min(args.steps, 10))
+    op.apply_host(xh, 0.0, prec=prec, out=oh)  # staging buffers allocated outside the timing
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        xd = xh.to(dev, non_blocking=True)
-        od = op.apply(xd, 0.0, prec=prec)
-        oh.copy_(od, non_blocking=True)
+        op.apply_host(xh, 0.0, prec=prec, out=oh)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": bytes_step / e2e_s / 1e9 * world, "unit": "GB/s",

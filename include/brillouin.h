@@ -119,6 +119,19 @@ bri_status bri_get_hops(bri_ctx *ctx, double *out, void *stream);
 bri_status bri_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int dagger,
                      bri_prec prec, void *stream);
 
+/* bri_apply with in and out in HOST memory: the library copies the input to
+ * its own device buffers in slabs of time slices, computes each slab of the
+ * output once the slab and its neighbours in t have arrived, and copies it
+ * back, so host-to-device copies, the stencil and device-to-host copies of
+ * different slabs overlap.  Page-locked host buffers (cudaHostAlloc or
+ * cudaHostRegister) are needed for the copies to run asynchronously; pageable
+ * buffers work but serialise.  Asynchronous on `stream`: the host buffers must
+ * stay valid, and out unread, until the stream has been synchronised.  The
+ * device staging buffers (2 x nrhs spinor fields) are owned by the context.
+ * Errors: as bri_apply. */
+bri_status bri_apply_host(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int dagger,
+                          bri_prec prec, void *stream);
+
 /* Hermitian overlap kernel H = gamma_5 (D_B - rho), D_B at m0 = 0 (the shifted
  * kernel of Sec. 7.4 entering Eq. def_over; rho = 1 there).  Same buffers and
  * errors as bri_apply. */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "bri_store_hops": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "bri_get_hops": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bri_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p]),
+    "bri_apply_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p]),
     "bri_apply_overlap_kernel": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_void_p]),
     "bri_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_int, c_int,
                           ctypes.POINTER(bri_solve_info), c_void_p]),

@@ -102,6 +102,19 @@ class Brillouin:
                                        _PREC[prec], _stream()))
         return out
 
+    def apply_host(self, psi, m0=0.0, dagger=False, prec="f64", out=None):
+        """D psi for a spinor in (pinned) host memory; the copies overlap the
+        stencil inside the library.  Returns after enqueueing on the current
+        stream: synchronise before reading out."""
+        dt = spinor_dtype(prec)
+        if psi.is_cuda or psi.dtype != dt or not psi.is_contiguous() or psi.numel() % (self.V * 12):
+            raise ValueError("psi must be a contiguous host %s tensor of nrhs*V*12 elements" % dt)
+        out = torch.empty_like(psi, pin_memory=psi.is_pinned()) if out is None else out
+        n = psi.numel() // (self.V * 12)
+        self._check(self.lib.bri_apply_host(self.ctx, out.data_ptr(), psi.data_ptr(), n, float(m0),
+                                            int(bool(dagger)), _PREC[prec], _stream()))
+        return out
+
     def overlap_kernel(self, psi, rho=1.0, prec="f64", out=None):
         n = self._spinor(psi, prec)
         out = torch.empty_like(psi) if out is None else out

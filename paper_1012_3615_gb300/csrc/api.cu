@@ -77,6 +77,8 @@ bri_status bri_create(const bri_lattice *lat, bri_ctx **out) {
         ctx->g.bc[mu] = lat->bc_sign[mu];
     }
     ctx->g.V = (int)V;
+    ctx->g.s0 = 0;
+    ctx->g.s1 = (int)V;
     {
         double lam[5], rho[5];
         for (int n = 0; n < 5; n++) {
@@ -98,6 +100,7 @@ bri_status bri_destroy(bri_ctx *ctx) {
     if (!ctx) return BRI_OK;
     bri_solver_free(ctx);
     bri_overlap_free(ctx);
+    bri_host_apply_free(ctx);
     cudaFree(ctx->clov64);
     cudaFree(ctx->clov32);
     cudaFree(ctx->U);
@@ -160,6 +163,21 @@ bri_status bri_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, double m
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, prec));
     return bri_dslash_impl(ctx, out, in, nrhs, m0, dagger ? 1 : 0, prec, as_stream(stream));
+}
+
+bri_status bri_apply_host(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int dagger, bri_prec prec,
+                          void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!out || !in) return bri_fail(ctx, BRI_EINVAL, "null spinor pointer");
+    if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
+    BRI_RETURN_IF(check_prec(ctx, prec));
+    const size_t bytes = (prec == BRI_F64 ? 16 : 8) * 12 * (size_t)ctx->g.V * nrhs;
+    const char *o = (const char *)out, *i = (const char *)in;
+    if (o < i + bytes && i < o + bytes) return bri_fail(ctx, BRI_EINVAL, "in and out overlap");
+    if (prec == BRI_F64 && !ctx->have64) return bri_fail(ctx, BRI_ESTATE, "FP64 hopping fields not built");
+    if (prec != BRI_F64 && !(prec == BRI_F32 ? ctx->f32 : ctx->f16).valid)
+        return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
+    return bri_apply_host_impl(ctx, out, in, nrhs, m0, dagger ? 1 : 0, prec, as_stream(stream));
 }
 
 bri_status bri_apply_overlap_kernel(bri_ctx *ctx, void *out, const void *in, int nrhs, double rho, bri_prec prec,

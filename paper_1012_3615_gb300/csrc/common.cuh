@@ -155,6 +155,9 @@ struct Geom {
     // (two slots each).  Null when the term is off.
     const double2 *clov64;
     const float4 *clov32;
+    // sites an apply covers, [s0, s1) (the whole lattice: 0, V); a t-slab of
+    // the lattice is a contiguous range
+    int s0, s1;
 };
 inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) {
     for (int n = 0; n < 5; n++) {

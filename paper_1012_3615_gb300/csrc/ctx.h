@@ -18,6 +18,7 @@ struct LinkStore {
 
 struct SolverWork;   // solver work spaces (solve.cu)
 struct OverlapWork;  // Lanczos / overlap state (overlap.cu)
+struct HostApplyWork;  // staging buffers and streams of bri_apply_host (hostapply.cu)
 
 struct bri_ctx {
     bri::Geom g;
@@ -29,6 +30,7 @@ struct bri_ctx {
     LinkStore p32, p16;  // site-pair interleaved copies (full / 2-row, even t extent)
     SolverWork *work = nullptr;
     OverlapWork *ov = nullptr;
+    HostApplyWork *hw = nullptr;
     double csw = 0.0;              // clover coefficient (0: no clover term)
     double2 *clov64 = nullptr;     // clover blocks, see Geom
     float4 *clov32 = nullptr;
@@ -85,6 +87,9 @@ bri_status bri_cdot_impl(bri_ctx *ctx, double *res, const void *a, const void *b
 bri_status bri_dp_levels(bri_ctx *ctx, void *A, const int *klist, const int start[6], cudaStream_t s);
 bri_status bri_force_impl(bri_ctx *ctx, double2 *dU, const double2 *chi, const double2 *psi, cudaStream_t s);
 void bri_overlap_free(bri_ctx *ctx);
+void bri_host_apply_free(bri_ctx *ctx);
+bri_status bri_apply_host_impl(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode,
+                               bri_prec prec, cudaStream_t user);
 bri_status bri_ape_impl(bri_ctx *ctx, double2 *V, const double2 *U, double alpha, int nsteps, cudaStream_t s);
 // (re)build the clover blocks from ctx->U with ctx->csw and switch the term on
 bri_status bri_clover_build_impl(bri_ctx *ctx, cudaStream_t s);

@@ -36,9 +36,28 @@ int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
     return prec == BRI_F64 ? 128 : (128 | 2048);
 }
 
+static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void *in, int nrhs, double m0, int mode,
+                              bri_prec prec, const int *skip, int threads, cudaStream_t s);
+
 bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
                           const int *skip, int threads, cudaStream_t s) {
-    const Geom &g = ctx->g;
+    return dslash_geom(ctx, ctx->g, out, in, nrhs, m0, mode, prec, skip, threads, s);
+}
+
+// only sites [s0, s1) of out are written (the plain kernels; the tiled and
+// site-pair kernels cover the whole lattice)
+bri_status bri_dslash_range(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
+                            int s0, int s1, cudaStream_t s) {
+    Geom g = ctx->g;
+    g.s0 = s0;
+    g.s1 = s1;
+    int threads = bri_dslash_threads(ctx, prec, nrhs);
+    if ((threads & 2047) == 0 || (threads >> 11) == 3) threads = prec == BRI_F64 ? 128 : (128 | 2048);
+    return dslash_geom(ctx, g, out, in, nrhs, m0, mode, prec, nullptr, threads, s);
+}
+
+static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void *in, int nrhs, double m0, int mode,
+                              bri_prec prec, const int *skip, int threads, cudaStream_t s) {
     const double diag = m0 + g.lamd[0];
     if (prec == BRI_F64) {
         if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "FP64 hopping fields not built");
@@ -48,7 +67,7 @@ bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, dou
         const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
         if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
         const LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
-        if ((threads >> 11) == 3 && ps.valid && !g.clov64) {
+        if ((threads >> 11) == 3 && ps.valid && !g.clov64 && g.s0 == 0 && g.s1 == g.V) {
             // site-pair kernel on the interleaved copy
             const int thr = (threads & 2047) ? (threads & 2047) : 64;
             const int H = g.V / 2;

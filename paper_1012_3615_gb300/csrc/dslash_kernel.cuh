@@ -494,8 +494,8 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
                          double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
     using R = typename RealOf<T>::R;
-    const int site = blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= g.V) return;
+    const int site = g.s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= g.s1) return;
     if (skip && skip[blockIdx.y]) return;
     const size_t off = (size_t)blockIdx.y * g.V * 12;
     in += off;
@@ -683,12 +683,12 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         int t = threads & 2047;
         if (t == 0) t = 128;
         if (t > max_c) t = max_c & ~31;
-        const dim3 grid((unsigned)((g.V + t - 1) / t), (unsigned)nrhs);
+        const dim3 grid((unsigned)((g.s1 - g.s0 + t - 1) / t), (unsigned)nrhs);
         k_dslash<LL, VC, true><<<grid, t, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         return;
     }
     if constexpr (sizeof(T) == 8) {
-        if ((threads & 2047) == 0 && (threads >> 11) == 0 && tiled_ok(g)) {
+        if ((threads & 2047) == 0 && (threads >> 11) == 0 && tiled_ok(g) && g.s0 == 0 && g.s1 == g.V) {
             static bool attr_set = false;
             if (!attr_set) {
                 cudaFuncSetAttribute(k_dslash_tiled<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
@@ -723,7 +723,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
             }
         }
         if (threads > max_threads[v]) threads = max_threads[v] & ~31;
-        grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
+        grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads), (unsigned)nrhs);
         if (v == 1) k_dslash<LL, 1><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 4) k_dslash<LL, 4><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 2)
@@ -738,7 +738,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
                 cudaFuncGetAttributes(&attr, k_dslash<LL, 0>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
         }
         if (threads > max_threads[0]) threads = max_threads[0] & ~31;
-        grid = dim3((unsigned)((g.V + threads - 1) / threads), (unsigned)nrhs);
+        grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads), (unsigned)nrhs);
         k_dslash<LL, 0><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
     }
 }

@@ -104,6 +104,8 @@ extern "C" bri_status bri_build_hops_noalloc(const bri_lattice *lat, const doubl
     if (V > BRI_NOALLOC_MAX_SITES)
         return fail(BRI_EINVAL, "bri_build_hops_noalloc: lattice volume exceeds the 4096-site scratch");
     g.V = (int)V;
+    g.s0 = 0;
+    g.s1 = (int)V;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= BRI_NOALLOC_MAX_DEVICES)
         return fail(BRI_ECUDA, "bri_build_hops_noalloc: no usable current device");

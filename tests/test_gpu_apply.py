@@ -237,3 +237,25 @@ def test_argument_errors(gpu):
         op.apply(big[1:].view(1, 81, 4, 3), prec="f32")  # 8-byte offset: not 16-byte aligned
     with pytest.raises(BriError):
         Brillouin((2, 4, 4, 4))
+
+
+@pytest.mark.parametrize("L", [(4, 3, 4, 3), (4, 4, 3, 6), (3, 4, 4, 12)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_host_buffers_match_device_apply(gpu, L, prec):
+    """bri_apply_host (slabs in t, copies overlapping the stencil) gives the
+    device apply bit for bit, pinned or pageable, D and D^dagger, 2 RHS."""
+    U = synth.random_su3_links(L, 0.4, 51)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32" if prec == "f32" else "f64", comp="full")
+    psi = synth.gaussian_spinor(L, 2, 52)
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    xd = torch.as_tensor(psi, device=gpu).to(dt).contiguous()
+    for pinned in (True, False):
+        xh = xd.cpu()
+        if pinned:
+            xh = xh.pin_memory()
+        for dag in (False, True):
+            want = op.apply(xd, 0.07, dagger=dag, prec=prec).cpu()
+            got = op.apply_host(xh, 0.07, dagger=dag, prec=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(got, want)
