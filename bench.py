@@ -367,7 +367,10 @@ def native(args, world, rank, local, pg):
                 sd = torch.complex128 if p == "f64" else torch.complex64
                 xx = synth.gaussian_spinor_torch(L, nr, SEED + 7, device=dev, dtype=sd)
                 oo = torch.empty_like(xx)
-                op.tune(p, nr)
+                if args.threads is not None:
+                    op.set_threads(p, nr, args.threads)
+                else:
+                    op.tune(p, nr)
                 t = time_apply(op, xx, oo, m, nr, 3 if p == "f64" else 10, 2, stream)
                 b = site_bytes(m, nr) * V
                 sweep["%s/n%d" % (m, nr)] = {"ms": t, "GB/s": b / (t * 1e-3) / 1e9,

@@ -494,10 +494,16 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
                          double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
     using R = typename RealOf<T>::R;
-    const int site = g.s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    // grid.x = site blocks x right-hand sides with the RHS fastest, so the blocks
+    // of all RHS over the same sites run together and read each link from DRAM
+    // once (the others hit L2)
+    const int nblk = (g.s1 - g.s0 + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int nr = (int)gridDim.x / nblk;
+    const int rhs = (int)blockIdx.x % nr;
+    const int site = g.s0 + ((int)blockIdx.x / nr) * (int)blockDim.x + (int)threadIdx.x;
     if (site >= g.s1) return;
-    if (skip && skip[blockIdx.y]) return;
-    const size_t off = (size_t)blockIdx.y * g.V * 12;
+    if (skip && skip[rhs]) return;
+    const size_t off = (size_t)rhs * g.V * 12;
     in += off;
     out += off;
     int x[4];
@@ -673,6 +679,20 @@ template <class LL>
 void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
                    const int *skip, int threads, cudaStream_t s) {
     using T = typename LL::T;
+    {
+        // grid.x holds site blocks x RHS: split the RHS so that it stays below 2^31
+        const size_t nbmax = (size_t)(g.s1 - g.s0 + 31) / 32;  // blocks at the smallest shape
+        const int rmax = (int)(0x7fffffffULL / nbmax < 65535ULL ? 0x7fffffffULL / nbmax : 65535ULL);
+        if (nrhs > rmax) {
+            const size_t field = sizeof(T) * 12 * (size_t)g.V;
+            for (int r0 = 0; r0 < nrhs; r0 += rmax) {
+                const int nr = nrhs - r0 < rmax ? nrhs - r0 : rmax;
+                dslash_launch(mode, ll, (const char *)in + r0 * field, (char *)out + r0 * field, nr, g, diag,
+                              skip ? skip + r0 : nullptr, threads, s);
+            }
+            return;
+        }
+    }
     if (g.clov64) {  // clover term on: the plain kernel (link prefetch variant for FP32) with the term
         constexpr int VC = sizeof(T) == 8 ? 1 : 0;
         static int max_c = 0;
@@ -683,7 +703,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         int t = threads & 2047;
         if (t == 0) t = 128;
         if (t > max_c) t = max_c & ~31;
-        const dim3 grid((unsigned)((g.s1 - g.s0 + t - 1) / t), (unsigned)nrhs);
+        const dim3 grid((unsigned)((g.s1 - g.s0 + t - 1) / t) * (unsigned)nrhs);
         k_dslash<LL, VC, true><<<grid, t, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         return;
     }
@@ -723,7 +743,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
             }
         }
         if (threads > max_threads[v]) threads = max_threads[v] & ~31;
-        grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads), (unsigned)nrhs);
+        grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads) * (unsigned)nrhs);
         if (v == 1) k_dslash<LL, 1><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 4) k_dslash<LL, 4><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 2)
@@ -738,7 +758,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
                 cudaFuncGetAttributes(&attr, k_dslash<LL, 0>) == cudaSuccess ? attr.maxThreadsPerBlock : 128;
         }
         if (threads > max_threads[0]) threads = max_threads[0] & ~31;
-        grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads), (unsigned)nrhs);
+        grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads) * (unsigned)nrhs);
         k_dslash<LL, 0><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
     }
 }
