@@ -523,7 +523,11 @@ def study_bench(dev):
     B (Sec. 6.4, Sec. 8): BiCGstab (FP64, true residual 1e-10, Z2 source) for
       each operator at its own "critical" bare mass -- where the smallest
       eigenvalue of D^dagger D is smallest on this volume -- and 0.1 above it:
-      iterations and time."""
+      iterations and time.
+    C (Sec. 7.2, 7.3): non-normality ||[D^dagger, D] eta|| and Ginsparg-Wilson
+      violation at that mass, on the links, after one APE step, and with the
+      clover term."""
+    import numpy as np
     import torch
 
     from paper_1012_3615_gb300 import Brillouin, synth
@@ -580,6 +584,32 @@ def study_bench(dev):
             r[tag] = {"m0": m0, "lambda_min": lm, "iters": inf[0]["iters"], "applies": 2 * inf[0]["iters"],
                       "status": inf[0]["status"], "true_resid": inf[0]["true_resid"],
                       "seconds": time.perf_counter() - t0}
+        # Sec. 7.2 / 7.3: non-normality ||(D^dag D - D D^dag) eta|| (mass independent)
+        # and the Ginsparg-Wilson violation ||(D g5 + g5 D - D g5 D) eta|| at the
+        # operator's own critical mass, for unit Gaussian eta, on these links and
+        # on one APE step (alpha = 0.72) with and without the clover term
+        g5 = torch.tensor([1, 1, -1, -1], dtype=torch.complex128, device=dev).view(1, 1, 4, 1)
+        etas = synth.gaussian_spinor_torch(L, 4, SEED + 14, device=dev)
+        etas = etas / etas.reshape(4, -1).norm(dim=1).view(4, 1, 1, 1)
+
+        def measures(m_gw):
+            nn, gw = [], []
+            for k in range(4):
+                e = etas[k:k + 1].contiguous()
+                De, Dde = op.apply(e, 0.0), op.apply(e, 0.0, dagger=True)
+                nn.append((op.apply(De, 0.0, dagger=True) - op.apply(Dde, 0.0)).norm().item())
+                Dm = op.apply(e, m_gw)
+                gw.append((op.apply((g5 * e).contiguous(), m_gw) + g5 * Dm
+                           - op.apply((g5 * Dm).contiguous(), m_gw)).norm().item())
+            return float(np.mean(nn)), float(np.mean(gw))
+
+        r["non_normality"], r["gw_violation_at_gap_minimum"] = measures(mstar)
+        V1 = op.ape_smear(U, 0.72, 1)
+        op.build_hops(V1, prec="f32", comp="full")
+        r["ape1_csw0"] = dict(zip(("non_normality", "gw_violation"), measures(mstar)))
+        op.set_clover(1.0)
+        r["ape1_csw1"] = dict(zip(("non_normality", "gw_violation"), measures(mstar)))
+        op.set_clover(0.0)
         out[name] = r
         del op
         torch.cuda.empty_cache()
@@ -590,7 +620,10 @@ def study_bench(dev):
         "solve_time_at_gap_minimum": br["solve_at_gap_minimum"]["seconds"] / w["solve_at_gap_minimum"]["seconds"],
         "lambda_max_m0_-1": br["ritz_m0_-1"]["lambda_max"] / w["ritz_m0_-1"]["lambda_max"],
         "cond_without_9": br["ritz_m0_-1"]["cond_without_9"] / w["ritz_m0_-1"]["cond_without_9"],
-        "sign_degree": br["overlap_rho_1_nlow_9"]["degree"] / w["overlap_rho_1_nlow_9"]["degree"]}
+        "sign_degree": br["overlap_rho_1_nlow_9"]["degree"] / w["overlap_rho_1_nlow_9"]["degree"],
+        "non_normality": br["non_normality"] / w["non_normality"],
+        "non_normality_ape1_csw1": br["ape1_csw1"]["non_normality"] / w["ape1_csw1"]["non_normality"],
+        "gw_violation": br["gw_violation_at_gap_minimum"] / w["gw_violation_at_gap_minimum"]}
     return out
 
 
