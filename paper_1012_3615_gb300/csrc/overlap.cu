@@ -353,7 +353,6 @@ struct OverlapWork {
     size_t part_cap = 0;
     double2 *h = nullptr;     // coefficients
     size_t h_cap = 0;
-    double *scal = nullptr;   // device scalars
 };
 
 static void free_ptr(void *p) {
@@ -370,7 +369,6 @@ void bri_overlap_free(bri_ctx *ctx) {
     for (auto &p : w->v32) free_ptr(p);
     free_ptr(w->part);
     free_ptr(w->h);
-    free_ptr(w->scal);
     free_ptr(w->cdef);
     delete w;
     ctx->ov = nullptr;
@@ -378,12 +376,24 @@ void bri_overlap_free(bri_ctx *ctx) {
 
 namespace {
 
+// device buffer released when it goes out of scope (cudaFree waits for the
+// work that may still use it)
+struct DevBuf {
+    void *p = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    template <typename T> T *as() const { return (T *)p; }
+};
+
 bri_status ensure_ov(bri_ctx *ctx) {
     if (ctx->ov) return BRI_OK;
     OverlapWork *w = new OverlapWork();
     ctx->ov = w;
     w->n = (size_t)ctx->g.V * 12;
-    BRI_TRY_CUDA(ctx, cudaMalloc(&w->scal, 64 * sizeof(double)));
     BRI_TRY_CUDA(ctx, cudaMalloc(&w->cdef, 2 * MAX_WANT * sizeof(double2)));
     return BRI_OK;
 }
@@ -465,94 +475,58 @@ bri_status lanczos(bri_ctx *ctx, double m0, int nlow, int mmax, double tol, cons
     const size_t n = o->n;
     mmax = (int)std::min<size_t>((size_t)mmax, n);
     if (nlow + 1 > mmax) return bri_fail(ctx, BRI_EINVAL, "max_krylov must exceed the number of wanted eigenpairs");
-    double2 *V = nullptr, *w = nullptr, *tmp = nullptr;
-    double *ab = nullptr, *tri_out = nullptr, *tri_work = nullptr;
-    unsigned char *tri_pw = nullptr;
-    double2 *S = nullptr;
     const int nw = nlow + 1;
-    bri_status st = BRI_OK;
-    auto fail_cuda = [&](cudaError_t e, const char *what) {
-        return bri_fail(ctx, e == cudaErrorMemoryAllocation ? BRI_ENOMEM : BRI_ECUDA,
-                        std::string("lanczos: ") + what + ": " + cudaGetErrorString(e));
-    };
-    cudaError_t e;
-    if ((e = cudaMalloc(&V, sizeof(double2) * n * (size_t)(mmax + 1))) != cudaSuccess) return fail_cuda(e, "basis");
-    auto cleanup = [&]() {
-        free_ptr(V); free_ptr(w); free_ptr(tmp); free_ptr(ab); free_ptr(tri_out); free_ptr(tri_work);
-        free_ptr(tri_pw); free_ptr(S);
-    };
-    if ((e = cudaMalloc(&w, sizeof(double2) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&tmp, sizeof(double2) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&ab, sizeof(double) * 2 * (size_t)(mmax + 2))) != cudaSuccess ||
-        (e = cudaMalloc(&tri_out, sizeof(double) * 2 * nw)) != cudaSuccess ||
-        (e = cudaMalloc(&tri_work, sizeof(double) * 5 * (size_t)mmax * nw)) != cudaSuccess ||
-        (e = cudaMalloc(&tri_pw, (size_t)mmax * nw)) != cudaSuccess ||
-        (nlow > 0 && Y && (e = cudaMalloc(&S, sizeof(double2) * (size_t)mmax * nlow)) != cudaSuccess)) {
-        cleanup();
-        return fail_cuda(e, "work space");
-    }
+    DevBuf Vb, wb, tmpb, abb, outb, workb, pwb, Sb;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&Vb.p, sizeof(double2) * n * (size_t)(mmax + 1)));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&wb.p, sizeof(double2) * n));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&tmpb.p, sizeof(double2) * n));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&abb.p, sizeof(double) * 2 * (size_t)(mmax + 2)));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&outb.p, sizeof(double) * 2 * nw));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&workb.p, sizeof(double) * 5 * (size_t)mmax * nw));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&pwb.p, (size_t)mmax * nw));
+    if (nlow > 0 && Y) BRI_TRY_CUDA(ctx, cudaMalloc(&Sb.p, sizeof(double2) * (size_t)mmax * nlow));
+    double2 *V = Vb.as<double2>(), *w = wb.as<double2>(), *tmp = tmpb.as<double2>(), *S = Sb.as<double2>();
+    double *ab = abb.as<double>(), *tri_out = outb.as<double>(), *tri_work = workb.as<double>();
+    unsigned char *tri_pw = pwb.as<unsigned char>();
     double *alpha = ab, *beta = ab + (mmax + 2);
     BRI_RETURN_IF(ensure_red(ctx, mmax + 1));
     double2 *h = o->h;
-#define LZ_TRY(x)                  \
-    do {                           \
-        st = (x);                  \
-        if (st != BRI_OK) {        \
-            cleanup();             \
-            return st;             \
-        }                          \
-    } while (0)
-#define LZ_CUDA(x, what)                          \
-    do {                                          \
-        cudaError_t e_ = (x);                     \
-        if (e_ != cudaSuccess) {                  \
-            cleanup();                            \
-            return fail_cuda(e_, what);           \
-        }                                         \
-    } while (0)
-    LZ_CUDA(cudaMemsetAsync(ab, 0, sizeof(double) * 2 * (size_t)(mmax + 2), s), "memset");
+    BRI_TRY_CUDA(ctx, cudaMemsetAsync(ab, 0, sizeof(double) * 2 * (size_t)(mmax + 2), s));
     k_rand_vec<<<vec_blocks(n), VT, 0, s>>>(w, n, seed);
-    LZ_TRY([&] { BRI_LAUNCHED(ctx); return BRI_OK; }());
-    LZ_TRY(project_out<double2>(ctx, w, Z, nz, h, s));
-    LZ_TRY(project_out<double2>(ctx, w, Z, nz, h, s));
-    LZ_TRY(normalize(ctx, V, w, beta, s));
+    BRI_LAUNCHED(ctx);
+    BRI_RETURN_IF(project_out<double2>(ctx, w, Z, nz, h, s));
+    BRI_RETURN_IF(project_out<double2>(ctx, w, Z, nz, h, s));
+    BRI_RETURN_IF(normalize(ctx, V, w, beta, s));
     std::vector<double> hout(2 * nw), hab(2 * (size_t)(mmax + 2));
     int m = 0, next_check = std::min(mmax, std::max(nw + 10, 20));
-    double theta_max = 0.0;
     res = LanczosResult();
     while (m < mmax) {
         double2 *vj = V + (size_t)m * n;
-        LZ_TRY(bri_dslash_impl(ctx, tmp, vj, 1, m0, 2, BRI_F64, s));
-        LZ_TRY(bri_dslash_impl(ctx, w, tmp, 1, m0, 2, BRI_F64, s));
+        BRI_RETURN_IF(bri_dslash_impl(ctx, tmp, vj, 1, m0, 2, BRI_F64, s));
+        BRI_RETURN_IF(bri_dslash_impl(ctx, w, tmp, 1, m0, 2, BRI_F64, s));
         res.applies += 2;
         // three-term step against v_{j-1}, v_j, then one Gram-Schmidt pass
         // against the whole basis (its coefficients are at rounding level)
-        {
-            const int j0 = m > 0 ? m - 1 : 0;
-            LZ_TRY(mdot<double2>(ctx, h, V + (size_t)j0 * n, n, m + 1 - j0, w, alpha + m, s));
-            LZ_TRY(maxpy<double2>(ctx, w, V + (size_t)j0 * n, n, h, m + 1 - j0, s));
-            LZ_TRY(mdot<double2>(ctx, h, V, n, m + 1, w, alpha + m, s));
-            LZ_TRY(maxpy<double2>(ctx, w, V, n, h, m + 1, s));
-        }
+        const int j0 = m > 0 ? m - 1 : 0;
+        BRI_RETURN_IF(mdot<double2>(ctx, h, V + (size_t)j0 * n, n, m + 1 - j0, w, alpha + m, s));
+        BRI_RETURN_IF(maxpy<double2>(ctx, w, V + (size_t)j0 * n, n, h, m + 1 - j0, s));
+        BRI_RETURN_IF(mdot<double2>(ctx, h, V, n, m + 1, w, alpha + m, s));
+        BRI_RETURN_IF(maxpy<double2>(ctx, w, V, n, h, m + 1, s));
         // deflation last: a component along Z left in the new basis vector would
         // grow from step to step (Z is an eigenspace of value 0 of P A P)
-        LZ_TRY(project_out<double2>(ctx, w, Z, nz, h, s));
-        LZ_TRY(normalize(ctx, V + (size_t)(m + 1) * n, w, beta + m + 1, s));
+        BRI_RETURN_IF(project_out<double2>(ctx, w, Z, nz, h, s));
+        BRI_RETURN_IF(normalize(ctx, V + (size_t)(m + 1) * n, w, beta + m + 1, s));
         m++;
         if (m < next_check && m < mmax) continue;
         next_check = std::min(mmax, m + std::max(10, m / 8));
         k_tri_ritz<<<1, 96, 0, s>>>(alpha, beta, m, nlow, 0, tri_out, nullptr, tri_work, tri_pw);
-        LZ_TRY([&] { BRI_LAUNCHED(ctx); return BRI_OK; }());
-        LZ_CUDA(cudaMemcpyAsync(hout.data(), tri_out, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, s), "copy");
-        LZ_CUDA(cudaMemcpyAsync(hab.data(), ab, sizeof(double) * 2 * (size_t)(mmax + 2), cudaMemcpyDeviceToHost, s),
-                "copy");
-        LZ_CUDA(cudaStreamSynchronize(s), "sync");
+        BRI_LAUNCHED(ctx);
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(hout.data(), tri_out, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, s));
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(hab.data(), ab, sizeof(double) * hab.size(), cudaMemcpyDeviceToHost, s));
+        BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         for (double v : hout)
-            if (!std::isfinite(v)) {
-                cleanup();
-                return bri_fail(ctx, BRI_ENAN, "lanczos: non-finite Ritz value");
-            }
-        theta_max = hout[nlow];
+            if (!std::isfinite(v)) return bri_fail(ctx, BRI_ENAN, "lanczos: non-finite Ritz value");
+        const double theta_max = hout[nlow];
         int nconv = 0;
         for (int k = 0; k < nlow; k++)
             if (hout[nw + k] <= tol * fabs(hout[k])) nconv++;
@@ -566,22 +540,18 @@ bri_status lanczos(bri_ctx *ctx, double m0, int nlow, int mmax, double tol, cons
         }
     }
     res.m = m;
-    if (nlow > 0 && Y) {
-        k_tri_ritz<<<1, 96, 0, s>>>(alpha, beta, m, nlow, 1, tri_out, S, tri_work, tri_pw);
-        LZ_TRY([&] { BRI_LAUNCHED(ctx); return BRI_OK; }());
+    const bool vectors = nlow > 0 && Y;
+    k_tri_ritz<<<1, 96, 0, s>>>(alpha, beta, m, nlow, vectors ? 1 : 0, tri_out, vectors ? S : nullptr, tri_work,
+                                tri_pw);
+    BRI_LAUNCHED(ctx);
+    if (vectors) {
         k_combine<double2><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(Y, n, V, n, S, m, m, nlow, n);
-        LZ_TRY([&] { BRI_LAUNCHED(ctx); return BRI_OK; }());
-    } else {
-        k_tri_ritz<<<1, 96, 0, s>>>(alpha, beta, m, nlow, 0, tri_out, nullptr, tri_work, tri_pw);
-        LZ_TRY([&] { BRI_LAUNCHED(ctx); return BRI_OK; }());
+        BRI_LAUNCHED(ctx);
     }
-    LZ_CUDA(cudaMemcpyAsync(hout.data(), tri_out, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, s), "copy");
-    LZ_CUDA(cudaStreamSynchronize(s), "sync");
-#undef LZ_TRY
-#undef LZ_CUDA
+    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(hout.data(), tri_out, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, s));
+    BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     res.theta.assign(hout.begin(), hout.begin() + nw);
     res.resid.assign(hout.begin() + nw, hout.end());
-    cleanup();
     return BRI_OK;
 }
 
@@ -594,37 +564,32 @@ bri_status build_poly(bri_ctx *ctx, double lo, double hi, double eps, std::vecto
     // little below that estimate and grow by 10% until the bound holds
     const double rate = std::log((std::sqrt(kappa) + 1.0) / (std::sqrt(kappa) - 1.0));
     int N = std::max(8, (int)std::floor(0.9 * std::log(1.0 / eps) / rate));
-    double *c = nullptr;
-    unsigned long long *e = nullptr;
+    DevBuf eb_, cb;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&eb_.p, sizeof(unsigned long long)));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&cb.p, sizeof(double) * MAX_DEGREE));
+    double *c = cb.as<double>();
+    unsigned long long *e = eb_.as<unsigned long long>();
     for (;;) {
-        if (N > MAX_DEGREE) {
-            free_ptr(c);
-            free_ptr(e);
+        if (N > MAX_DEGREE)
             return bri_fail(ctx, BRI_EINVAL,
                             "overlap setup: the polynomial would need degree > 60000; deflate more low modes or "
                             "relax eps");
-        }
-        free_ptr(c);
-        c = nullptr;
-        if (!e) BRI_TRY_CUDA(ctx, cudaMalloc(&e, sizeof(unsigned long long)));
-        BRI_TRY_CUDA(ctx, cudaMalloc(&c, sizeof(double) * N));
         k_cheb_coef<<<(N + 127) / 128, 128, 0, s>>>(c, N, lo, hi);
         BRI_LAUNCHED(ctx);
         BRI_TRY_CUDA(ctx, cudaMemsetAsync(e, 0, sizeof(unsigned long long), s));
         const int G = std::max(4096, 8 * N);
         k_cheb_err<<<(G + 127) / 128, 128, 0, s>>>(c, N, lo, hi, G, e);
         BRI_LAUNCHED(ctx);
-        unsigned long long eb = 0;
-        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(&eb, e, sizeof(eb), cudaMemcpyDeviceToHost, s));
+        unsigned long long bits = 0;
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(&bits, e, sizeof(bits), cudaMemcpyDeviceToHost, s));
         BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         double ev;
-        memcpy(&ev, &eb, sizeof(ev));
+        memcpy(&ev, &bits, sizeof(ev));
         if (ev <= eps) {
             coef.resize(N);
-            BRI_TRY_CUDA(ctx, cudaMemcpy(coef.data(), c, sizeof(double) * N, cudaMemcpyDeviceToHost));
+            BRI_TRY_CUDA(ctx, cudaMemcpyAsync(coef.data(), c, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+            BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
             err = ev;
-            free_ptr(c);
-            free_ptr(e);
             return BRI_OK;
         }
         N = std::max(N + 2, (int)std::ceil(N * 1.1));
@@ -762,64 +727,48 @@ bri_status bri_overlap_setup_impl(bri_ctx *ctx, double rho, int nlow, double eps
     double lo, hi;
     LanczosResult r1;
     if (nlow > 0) {
-        double2 *Y = nullptr, *HY = nullptr, *M = nullptr, *Q = nullptr, *C = nullptr;
-        BRI_TRY_CUDA(ctx, cudaMalloc(&Y, sizeof(double2) * n * nlow));
-        BRI_TRY_CUDA(ctx, cudaMalloc(&HY, sizeof(double2) * n * nlow));
-        BRI_TRY_CUDA(ctx, cudaMalloc(&M, sizeof(double2) * nlow * nlow * 4));
-        Q = M + nlow * nlow;
-        C = Q + nlow * nlow;
-        double2 *YHY = C + nlow * nlow;
+        DevBuf Yb, HYb, Mb;
+        BRI_TRY_CUDA(ctx, cudaMalloc(&Yb.p, sizeof(double2) * n * nlow));
+        BRI_TRY_CUDA(ctx, cudaMalloc(&HYb.p, sizeof(double2) * n * nlow));
+        BRI_TRY_CUDA(ctx, cudaMalloc(&Mb.p, sizeof(double2) * nlow * nlow * 4));
+        double2 *Y = Yb.as<double2>(), *HY = HYb.as<double2>(), *M = Mb.as<double2>();
+        double2 *Q = M + nlow * nlow, *C = Q + nlow * nlow, *YHY = C + nlow * nlow;
         BRI_TRY_CUDA(ctx, cudaMalloc(&o->Z, sizeof(double2) * n * nlow));
         BRI_TRY_CUDA(ctx, cudaMalloc(&o->lam, sizeof(double) * nlow));
-        bri_status st = lanczos(ctx, m0, nlow, max_krylov, tol, nullptr, 0, Y, 0x1012ull, r1, s);
+        BRI_RETURN_IF(lanczos(ctx, m0, nlow, max_krylov, tol, nullptr, 0, Y, 0x1012ull, r1, s));
         applies += r1.applies;
         kdim += r1.m;
-        if (st == BRI_OK && !r1.converged) st = bri_fail(ctx, BRI_ENOTCONV, "overlap setup: low modes of H^2 did not converge; raise max_krylov");
+        if (!r1.converged)
+            return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: low modes of H^2 did not converge; raise max_krylov");
         // Rayleigh-Ritz of H on the Ritz vectors of H^2
-        for (int b = 0; st == BRI_OK && b < nlow; b++) {
-            st = bri_dslash_impl(ctx, HY + (size_t)b * n, Y + (size_t)b * n, 1, m0, 2, BRI_F64, s);
+        for (int b = 0; b < nlow; b++) {
+            BRI_RETURN_IF(bri_dslash_impl(ctx, HY + (size_t)b * n, Y + (size_t)b * n, 1, m0, 2, BRI_F64, s));
             applies++;
-            if (st == BRI_OK) st = mdot<double2>(ctx, YHY + (size_t)b * nlow, Y, n, nlow, HY + (size_t)b * n, nullptr, s);
+            BRI_RETURN_IF(mdot<double2>(ctx, YHY + (size_t)b * nlow, Y, n, nlow, HY + (size_t)b * n, nullptr, s));
         }
-        if (st == BRI_OK) {
-            k_small_herm<<<1, 32, 0, s>>>(YHY, nlow, M, Q, C, o->lam);
-            ctx->launches++;
-            if (cudaGetLastError() != cudaSuccess) st = bri_fail(ctx, BRI_ECUDA, "overlap setup: launch failed");
-        }
-        if (st == BRI_OK) {
-            k_combine<double2><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(o->Z, n, Y, n, C, nlow, nlow, nlow, n);
-            ctx->launches++;
-            if (cudaGetLastError() != cudaSuccess) st = bri_fail(ctx, BRI_ECUDA, "overlap setup: launch failed");
-        }
+        k_small_herm<<<1, 32, 0, s>>>(YHY, nlow, M, Q, C, o->lam);
+        BRI_LAUNCHED(ctx);
+        k_combine<double2><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(o->Z, n, Y, n, C, nlow, nlow, nlow, n);
+        BRI_LAUNCHED(ctx);
         // residuals ||H z - lambda z|| of the deflated pairs
-        if (st == BRI_OK) {
-            std::vector<double> lam(nlow);
-            cudaMemcpyAsync(lam.data(), o->lam, sizeof(double) * nlow, cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-            for (int b = 0; st == BRI_OK && b < nlow; b++) {
-                st = bri_dslash_impl(ctx, HY, o->Z + (size_t)b * n, 1, m0, 2, BRI_F64, s);
-                applies++;
-                const double2 nl = make_double2(lam[b], 0.0);
-                if (st == BRI_OK) {
-                    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(o->h, &nl, sizeof(nl), cudaMemcpyHostToDevice, s));
-                    st = maxpy<double2>(ctx, HY, o->Z + (size_t)b * n, n, o->h, 1, s);
-                }
-                if (st == BRI_OK) {
-                    k_norm_part<<<DB, VT, 0, s>>>(HY, n, o->part);
-                    ctx->launches++;
-                    std::vector<double2> pp(DB);
-                    cudaMemcpyAsync(pp.data(), o->part, sizeof(double2) * DB, cudaMemcpyDeviceToHost, s);
-                    cudaStreamSynchronize(s);
-                    double sum = 0.0;
-                    for (auto &v : pp) sum += v.x;
-                    defl_resid = std::max(defl_resid, std::sqrt(sum));
-                }
-            }
+        std::vector<double> lam(nlow);
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(lam.data(), o->lam, sizeof(double) * nlow, cudaMemcpyDeviceToHost, s));
+        BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        std::vector<double2> coefs(nlow), parts(DB);
+        for (int b = 0; b < nlow; b++) coefs[b] = make_double2(lam[b], 0.0);
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(o->cdef, coefs.data(), sizeof(double2) * nlow, cudaMemcpyHostToDevice, s));
+        for (int b = 0; b < nlow; b++) {
+            BRI_RETURN_IF(bri_dslash_impl(ctx, HY, o->Z + (size_t)b * n, 1, m0, 2, BRI_F64, s));
+            applies++;
+            BRI_RETURN_IF(maxpy<double2>(ctx, HY, o->Z + (size_t)b * n, n, o->cdef + b, 1, s));
+            k_norm_part<<<DB, VT, 0, s>>>(HY, n, o->part);
+            BRI_LAUNCHED(ctx);
+            BRI_TRY_CUDA(ctx, cudaMemcpyAsync(parts.data(), o->part, sizeof(double2) * DB, cudaMemcpyDeviceToHost, s));
+            BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+            double sum = 0.0;
+            for (auto &v : parts) sum += v.x;
+            defl_resid = std::max(defl_resid, std::sqrt(sum));
         }
-        free_ptr(Y);
-        free_ptr(HY);
-        free_ptr(M);
-        BRI_RETURN_IF(st);
         o->nlow = nlow;
         // the rest of the spectrum of H^2: Lanczos on the deflated operator
         LanczosResult r2;
