@@ -223,11 +223,9 @@ bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double
     if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "the force of the clover term is not built (csw must be 0)");
     cudaStream_t s = as_stream(stream);
     const size_t n = (size_t)ctx->g.V * 12, bytes = n * sizeof(double2);
-    double2 *Z = nullptr, *X = nullptr, *Y = nullptr, *t = nullptr;
-    BRI_TRY_CUDA(ctx, cudaMalloc(&Z, bytes));
-    BRI_TRY_CUDA(ctx, cudaMalloc(&X, bytes));
-    BRI_TRY_CUDA(ctx, cudaMalloc(&Y, bytes));
-    BRI_TRY_CUDA(ctx, cudaMalloc(&t, bytes));
+    DevBuf work;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&work.p, 4 * bytes));
+    double2 *Z = work.as<double2>(), *X = Z + n, *Y = X + n, *t = Y + n;
     bri_status st = BRI_OK;
     bri_solve_info i1{}, i2{};
     do {
@@ -244,10 +242,6 @@ bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double
         st = bri_force_impl(ctx, (double2 *)dU, t, X, s);
     } while (0);
     cudaStreamSynchronize(s);
-    cudaFree(Z);
-    cudaFree(X);
-    cudaFree(Y);
-    cudaFree(t);
     if (info) *info = i2;
     if (st == BRI_OK && (i1.status != BRI_OK || i2.status != BRI_OK)) st = i1.status != BRI_OK ? i1.status : i2.status;
     return st;
@@ -400,9 +394,10 @@ const char *bri_last_error(bri_ctx *ctx) { return ctx ? ctx->err.c_str() : g_cre
 bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) {
     const size_t elt = prec == BRI_F64 ? 16 : 8;
     const size_t bytes = elt * 12 * (size_t)ctx->g.V * nrhs;
-    void *in = nullptr, *out = nullptr;
-    BRI_TRY_CUDA(ctx, cudaMalloc(&in, bytes));
-    BRI_TRY_CUDA(ctx, cudaMalloc(&out, bytes));
+    DevBuf inb, outb;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&inb.p, bytes));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&outb.p, bytes));
+    void *in = inb.p, *out = outb.p;
     BRI_TRY_CUDA(ctx, cudaMemsetAsync(in, 0, bytes, s));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -429,8 +424,6 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(in);
-    cudaFree(out);
     if (st != BRI_OK) return st;
     const std::string key = bri_tune_key(ctx, prec, nrhs);
     ctx->tune[key] = best;

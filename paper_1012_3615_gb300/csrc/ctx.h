@@ -67,6 +67,19 @@ bri_status bri_fail(bri_ctx *ctx, bri_status st, const std::string &msg);
 
 inline bool bri_aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// device buffer released when it goes out of scope (cudaFree waits for the
+// work that may still use it)
+struct DevBuf {
+    void *p = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    template <typename T> T *as() const { return (T *)p; }
+};
+
 // entry points implemented in the individual translation units
 bri_status bri_hops_build_impl(bri_ctx *ctx, cudaStream_t s);
 bri_status bri_hops_store_impl(bri_ctx *ctx, bri_prec prec, bri_comp comp, cudaStream_t s);

@@ -376,19 +376,6 @@ void bri_overlap_free(bri_ctx *ctx) {
 
 namespace {
 
-// device buffer released when it goes out of scope (cudaFree waits for the
-// work that may still use it)
-struct DevBuf {
-    void *p = nullptr;
-    DevBuf() = default;
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    template <typename T> T *as() const { return (T *)p; }
-};
-
 bri_status ensure_ov(bri_ctx *ctx) {
     if (ctx->ov) return BRI_OK;
     OverlapWork *w = new OverlapWork();

@@ -190,25 +190,19 @@ bri_status bri_ape_impl(bri_ctx *ctx, double2 *V, const double2 *U, double alpha
         BRI_TRY_CUDA(ctx, cudaMemcpyAsync(V, U, bytes, cudaMemcpyDeviceToDevice, s));
         return BRI_OK;
     }
-    double2 *tmp = nullptr;
-    if (nsteps > 1) BRI_TRY_CUDA(ctx, cudaMalloc(&tmp, bytes));
+    DevBuf tmpb;
+    if (nsteps > 1) BRI_TRY_CUDA(ctx, cudaMalloc(&tmpb.p, bytes));
+    double2 *tmp = tmpb.as<double2>();
     const unsigned nb = (unsigned)((ctx->g.V + 127) / 128);
     const double2 *src = U;
     for (int k = 0; k < nsteps; k++) {
         // the last step lands in V: alternate so that it does
         double2 *dst = ((nsteps - 1 - k) % 2 == 0) ? V : tmp;
         k_ape<<<dim3(nb, 4), 128, 0, s>>>(src, dst, ctx->g, alpha);
-        ctx->launches++;
-        if (cudaGetLastError() != cudaSuccess) {
-            if (tmp) cudaFree(tmp);
-            return bri_fail(ctx, BRI_ECUDA, "bri_ape_smear: launch failed");
-        }
+        BRI_LAUNCHED(ctx);
         src = dst;
     }
-    if (tmp) {
-        BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-        cudaFree(tmp);
-    }
+    if (tmp) BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));  // the temporary is freed on return
     return BRI_OK;
 }
 
