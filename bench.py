@@ -360,7 +360,7 @@ def native(args, world, rank, local, pg):
     if args.sweep:
         sweep = {}
         for m in ["f64-full", "f32-full", "f32-2row", "f32-8param", "f16-full", "f16-2row", "f16-8param"]:
-            for nr in ([1] if m.startswith("f64") else [1, 4, 12]):
+            for nr in ([1] if m.startswith("f64") else [1, 4, 12, 24]):
                 p, c = m.split("-")
                 if p != "f64":
                     op.store_hops(p, c)

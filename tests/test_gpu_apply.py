@@ -259,3 +259,15 @@ def test_apply_host_buffers_match_device_apply(gpu, L, prec):
             got = op.apply_host(xh, 0.07, dagger=dag, prec=prec)
             torch.cuda.synchronize()
             assert torch.equal(got, want)
+
+
+def test_many_right_hand_sides(gpu):
+    """1000 right-hand sides in one launch on a 3^4 lattice (grid of site
+    blocks x RHS): every RHS equals its own single apply."""
+    L = (3, 3, 3, 3)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(synth.random_su3_links(L, 0.5, 71), device=gpu), prec="f32")
+    x = synth.gaussian_spinor_torch(L, 1000, 72, device=gpu).to(torch.complex64)
+    many = op.apply(x, 0.2, prec="f32")
+    for r in (0, 1, 499, 998, 999):
+        assert torch.equal(many[r:r + 1], op.apply(x[r:r + 1].contiguous(), 0.2, prec="f32"))
