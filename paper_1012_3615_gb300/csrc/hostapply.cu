@@ -17,7 +17,7 @@ bri_status bri_dslash_range(bri_ctx *ctx, void *out, const void *in, int nrhs, d
 struct HostApplyWork {
     void *din = nullptr, *dout = nullptr;
     size_t cap = 0;
-    cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+    cudaStream_t h2d = nullptr, comp[2] = {nullptr, nullptr}, d2h = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_out;
     cudaEvent_t start = nullptr, done = nullptr;
 };
@@ -25,7 +25,7 @@ struct HostApplyWork {
 void bri_host_apply_free(bri_ctx *ctx) {
     HostApplyWork *w = ctx->hw;
     if (!w) return;
-    for (cudaStream_t s : {w->h2d, w->comp, w->d2h})
+    for (cudaStream_t s : {w->h2d, w->comp[0], w->comp[1], w->d2h})
         if (s) cudaStreamSynchronize(s);
     if (w->din) cudaFree(w->din);
     if (w->dout) cudaFree(w->dout);
@@ -33,7 +33,7 @@ void bri_host_apply_free(bri_ctx *ctx) {
     for (auto e : w->ev_out) cudaEventDestroy(e);
     if (w->start) cudaEventDestroy(w->start);
     if (w->done) cudaEventDestroy(w->done);
-    for (cudaStream_t s : {w->h2d, w->comp, w->d2h})
+    for (cudaStream_t s : {w->h2d, w->comp[0], w->comp[1], w->d2h})
         if (s) cudaStreamDestroy(s);
     delete w;
     ctx->hw = nullptr;
@@ -46,7 +46,7 @@ static bri_status ensure_host_work(bri_ctx *ctx, size_t bytes) {
     if (!w) {
         w = new HostApplyWork();
         ctx->hw = w;
-        for (cudaStream_t *s : {&w->h2d, &w->comp, &w->d2h})
+        for (cudaStream_t *s : {&w->h2d, &w->comp[0], &w->comp[1], &w->d2h})
             BRI_TRY_CUDA(ctx, cudaStreamCreateWithFlags(s, cudaStreamNonBlocking));
         w->ev_in.resize(MAX_SLABS);
         w->ev_out.resize(MAX_SLABS);
@@ -57,7 +57,7 @@ static bri_status ensure_host_work(bri_ctx *ctx, size_t bytes) {
     }
     if (w->cap < bytes) {
         // earlier calls may still be reading or writing the staging buffers
-        for (cudaStream_t s : {w->h2d, w->comp, w->d2h}) BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        for (cudaStream_t s : {w->h2d, w->comp[0], w->comp[1], w->d2h}) BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         if (w->din) cudaFree(w->din);
         if (w->dout) cudaFree(w->dout);
         w->din = w->dout = nullptr;
@@ -83,7 +83,8 @@ bri_status bri_apply_host_impl(bri_ctx *ctx, void *out, const void *in, int nrhs
     for (int k = 0; k <= K; k++) tb[k] = (int)((long)k * Lt / K);
     // work enqueued on the caller's stream before this call comes first
     BRI_TRY_CUDA(ctx, cudaEventRecord(w->start, user));
-    for (cudaStream_t s : {w->h2d, w->comp, w->d2h}) BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(s, w->start, 0));
+    for (cudaStream_t s : {w->h2d, w->comp[0], w->comp[1], w->d2h})
+        BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(s, w->start, 0));
     for (int r = 0; r < nrhs; r++) {
         char *din = (char *)w->din + r * per_rhs, *dout = (char *)w->dout + r * per_rhs;
         const char *hin = (const char *)in + r * per_rhs;
@@ -95,11 +96,14 @@ bri_status bri_apply_host_impl(bri_ctx *ctx, void *out, const void *in, int nrhs
         }
         for (int i = 1; i <= K; i++) {
             const int k = i % K;
+            // slabs alternate between two compute streams so that the tail of one
+            // slab's grid overlaps the start of the next
+            cudaStream_t cs = w->comp[i & 1];
             const int need[3] = {(k + K - 1) % K, k, (k + 1) % K};
-            for (int nb : need) BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(w->comp, w->ev_in[nb], 0));
+            for (int nb : need) BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(cs, w->ev_in[nb], 0));
             BRI_RETURN_IF(bri_dslash_range(ctx, dout, din, 1, m0, mode, prec, (int)(tb[k] * S3), (int)(tb[k + 1] * S3),
-                                           w->comp));
-            BRI_TRY_CUDA(ctx, cudaEventRecord(w->ev_out[k], w->comp));
+                                           cs));
+            BRI_TRY_CUDA(ctx, cudaEventRecord(w->ev_out[k], cs));
             BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(w->d2h, w->ev_out[k], 0));
             const size_t o = (size_t)tb[k] * S3 * 12 * elt, n = (size_t)(tb[k + 1] - tb[k]) * S3 * 12 * elt;
             BRI_TRY_CUDA(ctx, cudaMemcpyAsync(hout + o, dout + o, n, cudaMemcpyDeviceToHost, w->d2h));
@@ -108,7 +112,8 @@ bri_status bri_apply_host_impl(bri_ctx *ctx, void *out, const void *in, int nrhs
     // the next call's input copies must not overwrite slabs still being read
     BRI_TRY_CUDA(ctx, cudaEventRecord(w->done, w->d2h));
     BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(w->h2d, w->done, 0));
-    BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(w->comp, w->done, 0));
+    BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(w->comp[0], w->done, 0));
+    BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(w->comp[1], w->done, 0));
     BRI_TRY_CUDA(ctx, cudaStreamWaitEvent(user, w->done, 0));
     return BRI_OK;
 }
