@@ -115,26 +115,18 @@ BRI_D void phase_solve(const double s[3], double phi, double th[3]) {
     const double c = -phi;
     const double M = asin(fmin(1.0, s[2] / s[0])) + asin(fmin(1.0, s[2] / s[1])) + 0.5 * PI;
     double best = -1e300;
-    bool found = false;
-    for (int rep = -1; rep <= 1; rep++) {
-        double t = c + 2.0 * PI * rep;
-        if (fabs(t) > M) continue;
-        double kappa = solve_branch_a(s, t);
-        double f = 0, tt[3];
+    // Branch A: of the targets t = -phi + 2 pi k only the one of smallest |t|
+    // (k = 0, phi in (-pi, pi]) can be the maximum -- the root kappa(t) grows in
+    // |kappa| with |t| and the objective sum_i sqrt(s_i^2 - kappa^2) falls with
+    // |kappa| -- and if it is out of reach (|t| > M) so are the others.
+    if (fabs(c) <= M) {
+        const double kappa = solve_branch_a(s, c);
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            tt[i] = asin(fmin(1.0, fmax(-1.0, kappa / s[i])));
-            f += sqrt(fmax(s[i] * s[i] - kappa * kappa, 0.0));
-        }
+        for (int i = 0; i < 3; i++) th[i] = asin(fmin(1.0, fmax(-1.0, kappa / s[i])));
         // place the rounding residue of the constraint on theta_3
-        tt[2] = t - tt[0] - tt[1];
-        if (f > best) {
-            best = f;
-            found = true;
-            th[0] = tt[0]; th[1] = tt[1]; th[2] = tt[2];
-        }
+        th[2] = c - th[0] - th[1];
+        return;
     }
-    if (found) return;
     // branch B: theta_3 = pi - asin(kappa/s_3); the target lies in (M, 2 pi - M)
     double t = c < 0 ? c + 2.0 * PI : c;
     const int NS = 64;
