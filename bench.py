@@ -443,7 +443,15 @@ def rows_bench(dev):
     dU, info = op.force_inverse(chi, m0=0.0, tol=1e-10)
     torch.cuda.synchronize()
     out["force_inverse_12x12x12x12"] = {"seconds": time.perf_counter() - t0, "iters_second_solve": info["iters"],
-                                        "status": info["status"]}
+                                        "status": info["status"], "solves": "FP64 BiCGstab"}
+    op.store_hops("f32", "full")
+    t0 = time.perf_counter()
+    dU, info = op.force_inverse(chi, m0=0.0, tol=1e-10)
+    torch.cuda.synchronize()
+    out["force_inverse_12x12x12x12_mixed"] = {"seconds": time.perf_counter() - t0,
+                                              "iters_second_solve": info["iters"],
+                                              "outer_second_solve": info["outer_iters"], "status": info["status"],
+                                              "solves": "FP64 defect correction around FP32 BiCGstab"}
     return out
 
 

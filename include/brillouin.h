@@ -174,7 +174,9 @@ bri_status bri_force(bri_ctx *ctx, double *dU, const double *chi, const double *
                      int recompute_hops, void *stream);
 
 /* dU += d( phi^dagger (D^dagger D)^{-1} phi ) / dU = -2 d Re(Y^dagger D X)/dU
- * with X = (D^dagger D)^{-1} phi, Y = D X (both solved in FP64 to tol).
+ * with X = (D^dagger D)^{-1} phi, Y = D X, both solved to the true FP64
+ * relative residual tol: by FP64 defect correction around FP32 BiCGstab when
+ * FP32 hopping fields are stored (bri_solve mode 1), else by FP64 BiCGstab.
  * phi: device [V][4][3] complex128.  info (host, may be null) receives the
  * second solve's data.  Synchronises the stream. */
 bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double m0, double tol,

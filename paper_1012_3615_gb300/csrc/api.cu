@@ -228,14 +228,17 @@ bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double
     double2 *Z = work.as<double2>(), *X = Z + n, *Y = X + n, *t = Y + n;
     bri_status st = BRI_OK;
     bri_solve_info i1{}, i2{};
+    // FP64 defect correction around FP32 BiCGstab when FP32 fields are stored
+    // (same FP64 true residual, far fewer FP64 applies), else FP64 BiCGstab
+    const int mode = ctx->f32.valid ? 1 : 0;
     do {
         // D^dagger Z = phi  <=>  D (g5 Z) = g5 phi
         if ((st = gamma5_scale(ctx, t, (const double2 *)phi, 1, 0.0, s)) != BRI_OK) break;
         BRI_TRY_CUDA(ctx, cudaMemsetAsync(Z, 0, bytes, s));
-        if ((st = bri_solve_impl(ctx, (double *)Z, (const double *)t, 1, m0, tol, maxit, 0, &i1, s)) != BRI_OK) break;
+        if ((st = bri_solve_impl(ctx, (double *)Z, (const double *)t, 1, m0, tol, maxit, mode, &i1, s)) != BRI_OK) break;
         if ((st = gamma5_scale(ctx, t, Z, 1, 0.0, s)) != BRI_OK) break;  // Z = g5 w
         BRI_TRY_CUDA(ctx, cudaMemsetAsync(X, 0, bytes, s));
-        if ((st = bri_solve_impl(ctx, (double *)X, (const double *)t, 1, m0, tol, maxit, 0, &i2, s)) != BRI_OK) break;
+        if ((st = bri_solve_impl(ctx, (double *)X, (const double *)t, 1, m0, tol, maxit, mode, &i2, s)) != BRI_OK) break;
         if ((st = bri_dslash_impl(ctx, Y, X, 1, m0, 0, BRI_F64, s)) != BRI_OK) break;
         // -2 d Re(Y^dagger D X)/dU: scale Y by -2
         if ((st = gamma5_scale(ctx, t, Y, 0, -2.0, s)) != BRI_OK) break;

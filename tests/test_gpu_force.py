@@ -34,8 +34,10 @@ def test_force_accumulates(gpu):
     assert torch.allclose(b, 2 * a, rtol=0, atol=1e-13 * a.abs().max().item())
 
 
-def test_force_inverse_matches_oracle(gpu):
-    """d(phi^dagger (D^dagger D)^{-1} phi)/dU = -2 d Re(Y^dagger D X)/dU."""
+@pytest.mark.parametrize("f32", [False, True])
+def test_force_inverse_matches_oracle(gpu, f32):
+    """d(phi^dagger (D^dagger D)^{-1} phi)/dU = -2 d Re(Y^dagger D X)/dU; with FP32
+    fields stored the two solves run as FP64 defect correction."""
     L = (3, 3, 3, 4)
     m0 = 0.1
     U = synth.random_su3_links(L, 0.3, 5)
@@ -48,8 +50,9 @@ def test_force_inverse_matches_oracle(gpu):
     Y = oracle.apply(L, AP, W, m0, X)
     ref = oracle.force(L, AP, U, m0, -2 * Y, X)
     op = Brillouin(L, AP)
-    op.build_hops(torch.as_tensor(U, device=gpu))
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32" if f32 else "f64")
     dU, info = op.force_inverse(torch.as_tensor(phi, device=gpu), m0=m0, tol=1e-13)
+    assert info["status"] == "BRI_OK" and (info["outer_iters"] > 0) == f32, info
     assert np.abs(dU.cpu().numpy() - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
