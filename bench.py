@@ -531,7 +531,7 @@ def study_bench(dev):
     """Comparisons between members of the operator class on one synthetic field
     (12^4, links exp(i0.3H), antiperiodic t), Wilson against Brillouin:
     A (Sec. 7.4): smallest, 10th and largest eigenvalue of D^dagger D at
-      m0 = -1 (the shifted overlap kernel, rho = 1), the condition numbers with
+      m0 = -1 (the shifted overlap kernel, rho = 1; FP32 Lanczos, tol 1e-6), the condition numbers with
       and without the 9 lowest modes, and the sign-function polynomial degree
       for eps = 1e-10 after deflating 9 modes (FP32 polynomial), with the time
       of one overlap application.
@@ -558,7 +558,7 @@ def study_bench(dev):
         op.set_weights(*WEIGHTS[name])
         op.build_hops(U, prec="f32", comp="full")
         r = {}
-        ev, lmax, info = op.eigs_ddag_d(10, m0=-1.0, max_krylov=3000, tol=1e-8)
+        ev, lmax, info = op.eigs_ddag_d(10, m0=-1.0, max_krylov=3000, tol=1e-6, prec="f32")
         r["ritz_m0_-1"] = {"lambda_1": ev[0], "lambda_10": ev[9], "lambda_max": lmax,
                            "cond": lmax / ev[0], "cond_without_9": lmax / ev[9],
                            "krylov_dim": info["krylov_dim"], "status": info["status"]}
@@ -570,7 +570,7 @@ def study_bench(dev):
         r["overlap_rho_1_nlow_9"] = dict(ov, apply_seconds=time.perf_counter() - t0)
 
         def lmin(m0):
-            e, _, _ = op.eigs_ddag_d(1, m0=m0, max_krylov=2000, tol=1e-2)
+            e, _, _ = op.eigs_ddag_d(1, m0=m0, max_krylov=2000, tol=1e-2, prec="f32")
             return e[0]
 
         # the bare mass where the smallest eigenvalue of D^dagger D is smallest

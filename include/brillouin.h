@@ -270,13 +270,16 @@ typedef struct {
  * evals: host, nev doubles, the nev smallest eigenvalues ascending; lmax: host
  * double or NULL, the largest; evecs: device [nev][V][4][3] complex128 or NULL,
  * the Ritz vectors (unit norm).  Converged when every residual estimate is
- * below tol x its Ritz value.  Uses the FP64 hopping fields and the class
- * weights set on ctx.  Synchronises the stream.  nev in [1, 64], max_krylov
- * in [nev + 1, 12 V].  Errors: BRI_EINVAL, BRI_ESTATE (no FP64 fields),
- * BRI_ENOTCONV (max_krylov reached; evals hold the last Ritz values),
- * BRI_ENOMEM. */
+ * below tol x its Ritz value.  prec: BRI_F64 (FP64 fields, vectors and
+ * arithmetic), or BRI_F32 / BRI_F16 (the Lanczos vectors and applies in FP32
+ * with the FP32 / FP16 fields, FP64 sums: about 100x faster on this GPU, Ritz
+ * values good to about 1e-7 relative, so tol below ~1e-6 cannot be met).
+ * Uses the class weights set on ctx.  Synchronises the stream.  nev in
+ * [1, 64], max_krylov in [nev + 1, 12 V].  Errors: BRI_EINVAL, BRI_ESTATE (no
+ * fields of that precision), BRI_ENOTCONV (max_krylov reached; evals hold the
+ * last Ritz values), BRI_ENOMEM. */
 bri_status bri_eigs_ddag_d(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0,
-                           int max_krylov, double tol, bri_eig_info *info, void *stream);
+                           int max_krylov, double tol, bri_prec prec, bri_eig_info *info, void *stream);
 
 typedef struct {
     int nlow;          /* deflated eigenpairs of H */
@@ -302,7 +305,10 @@ typedef struct {
  * whose sign error
  * max |1 - sqrt(x) p(x)| is <= eps.  prec: arithmetic of the polynomial
  * (BRI_F64, or BRI_F32 / BRI_F16 with the FP32 / FP16 hopping fields of that
- * precision; deflation and the final sum stay FP64).  State is kept in ctx
+ * precision).  With BRI_F32 / BRI_F16 the Lanczos runs, the Rayleigh-Ritz step
+ * and the deflation vectors use that precision too (tol is raised to at least
+ * 1e-6; the deflated eigenvalues are then good to about 1e-7), while the
+ * projection of the input and the final sum stay FP64.  State is kept in ctx
  * until the next setup; changing the links or weights invalidates it.
  * Synchronises the stream.  rho in (0, 2), nlow in [0, 64], eps in
  * [1e-14, 0.1].  Errors: BRI_EINVAL (also when the degree would exceed

@@ -76,7 +76,7 @@ SIGNATURES = {
     "bri_ape_smear": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]),
     "bri_set_clover": (c_int, [c_void_p, c_double, c_void_p]),
     "bri_eigs_ddag_d": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double), c_void_p, c_int,
-                                c_double, c_int, c_double, ctypes.POINTER(bri_eig_info), c_void_p]),
+                                c_double, c_int, c_double, c_int, ctypes.POINTER(bri_eig_info), c_void_p]),
     "bri_overlap_setup": (c_int, [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int,
                                   ctypes.POINTER(bri_overlap_info), c_void_p]),
     "bri_overlap_modes": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p]),

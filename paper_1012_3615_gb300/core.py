@@ -193,7 +193,7 @@ class Brillouin:
         self._check(self.lib.bri_set_clover(self.ctx, float(csw), _stream()))
 
     # ---- spectra and the overlap operator (Sec. 7) -----------------------------------
-    def eigs_ddag_d(self, nev, m0=0.0, max_krylov=500, tol=1e-10, vectors=False):
+    def eigs_ddag_d(self, nev, m0=0.0, max_krylov=500, tol=1e-10, vectors=False, prec="f64"):
         """nev smallest and the largest eigenvalue of D(m0)^dagger D(m0) (Lanczos
         in the library).  Returns (evals, lmax, info) or (evals, lmax, vecs, info)."""
         ev = (ctypes.c_double * nev)()
@@ -201,7 +201,8 @@ class Brillouin:
         info = abi.bri_eig_info()
         vecs = torch.empty((nev, self.V, 4, 3), dtype=torch.complex128, device="cuda") if vectors else None
         st = self.lib.bri_eigs_ddag_d(self.ctx, ev, ctypes.byref(lmax), _ptr(vecs) if vectors else None, int(nev),
-                                      float(m0), int(max_krylov), float(tol), ctypes.byref(info), _stream())
+                                      float(m0), int(max_krylov), float(tol), _PREC[prec], ctypes.byref(info),
+                                      _stream())
         if st not in (0, abi.BRI_ENOTCONV):
             self._check(st)
         out = (list(ev), lmax.value) + ((vecs,) if vectors else ()) + (info.as_dict(),)

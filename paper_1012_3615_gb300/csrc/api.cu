@@ -307,7 +307,7 @@ bri_status bri_set_clover(bri_ctx *ctx, double csw, void *stream) {
 
 // ---- spectra and the overlap operator ------------------------------------------------
 bri_status bri_eigs_ddag_d(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0,
-                           int max_krylov, double tol, bri_eig_info *info, void *stream) {
+                           int max_krylov, double tol, bri_prec prec, bri_eig_info *info, void *stream) {
     if (!ctx) return BRI_EINVAL;
     if (!evals) return bri_fail(ctx, BRI_EINVAL, "evals must be a host array of nev doubles");
     if (evecs && !bri_aligned16(evecs)) return bri_fail(ctx, BRI_EINVAL, "evecs must be 16-byte aligned");
@@ -315,8 +315,11 @@ bri_status bri_eigs_ddag_d(bri_ctx *ctx, double *evals, double *lmax, double *ev
     if (max_krylov <= nev || (size_t)max_krylov > 12 * (size_t)ctx->g.V)
         return bri_fail(ctx, BRI_EINVAL, "max_krylov must be in [nev + 1, 12 V]");
     if (!(tol > 0) || !std::isfinite(m0)) return bri_fail(ctx, BRI_EINVAL, "tol must be > 0 and m0 finite");
+    BRI_RETURN_IF(check_prec(ctx, prec));
     if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
-    return bri_eigs_impl(ctx, evals, lmax, evecs, nev, m0, max_krylov, tol, info, as_stream(stream));
+    if ((prec == BRI_F32 && !ctx->f32.valid) || (prec == BRI_F16 && !ctx->f16.valid))
+        return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
+    return bri_eigs_impl(ctx, evals, lmax, evecs, nev, m0, max_krylov, tol, prec, info, as_stream(stream));
 }
 
 bri_status bri_overlap_setup(bri_ctx *ctx, double rho, int nlow, double eps, int max_krylov, double tol,

@@ -107,7 +107,7 @@ bri_status bri_ape_impl(bri_ctx *ctx, double2 *V, const double2 *U, double alpha
 // (re)build the clover blocks from ctx->U with ctx->csw and switch the term on
 bri_status bri_clover_build_impl(bri_ctx *ctx, cudaStream_t s);
 bri_status bri_eigs_impl(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0, int max_krylov,
-                         double tol, bri_eig_info *info, cudaStream_t s);
+                         double tol, bri_prec prec, bri_eig_info *info, cudaStream_t s);
 bri_status bri_overlap_setup_impl(bri_ctx *ctx, double rho, int nlow, double eps, int max_krylov, double tol,
                                   bri_prec prec, bri_overlap_info *info, cudaStream_t s);
 bri_status bri_overlap_modes_impl(bri_ctx *ctx, double *lambda, double *vecs, cudaStream_t s);

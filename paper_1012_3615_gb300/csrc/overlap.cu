@@ -74,10 +74,22 @@ template <typename T>
 __global__ void k_mdot_part(const T *__restrict__ Vb, size_t ldv, const T *__restrict__ w, size_t n, double2 *part) {
     const T *v = Vb + (size_t)blockIdx.y * ldv;
     double2 acc = make_double2(0.0, 0.0);
-    for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
-        const double2 a = d2(v[i]), b = d2(w[i]);
-        acc.x += a.x * b.x + a.y * b.y;
-        acc.y += a.x * b.y - a.y * b.x;
+    if constexpr (sizeof(T) == 8) {
+        // FP32 vectors: FP32 products per thread (FP64 is 1/64 of the FP32 rate),
+        // FP64 across threads and blocks
+        float2 f = make_float2(0.f, 0.f);
+        for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
+            const T a = v[i], b = w[i];
+            f.x = fmaf(a.x, b.x, fmaf(a.y, b.y, f.x));
+            f.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, f.y));
+        }
+        acc = make_double2(f.x, f.y);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
+            const double2 a = d2(v[i]), b = d2(w[i]);
+            acc.x += a.x * b.x + a.y * b.y;
+            acc.y += a.x * b.y - a.y * b.x;
+        }
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
@@ -99,17 +111,26 @@ template <typename T>
 __global__ void k_maxpy(T *__restrict__ w, const T *__restrict__ Vb, size_t ldv, const double2 *__restrict__ h, int m,
                         size_t n) {
     for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
-        double2 acc = d2(w[i]);
-        int j = 0;
-        for (; j + 4 <= m; j += 4) {
-            double2 v[4];
+        if constexpr (sizeof(T) == 8) {  // FP32 vectors: FP32 arithmetic
+            float2 acc = w[i];
+            for (int j = 0; j < m; j++) {
+                const float2 c = make_float2((float)h[j].x, (float)h[j].y), v = Vb[(size_t)j * ldv + i];
+                acc = csub(acc, cmul(c, v));
+            }
+            w[i] = acc;
+        } else {
+            double2 acc = d2(w[i]);
+            int j = 0;
+            for (; j + 4 <= m; j += 4) {
+                double2 v[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) v[q] = d2(Vb[(size_t)(j + q) * ldv + i]);
+                for (int q = 0; q < 4; q++) v[q] = d2(Vb[(size_t)(j + q) * ldv + i]);
 #pragma unroll
-            for (int q = 0; q < 4; q++) acc = csub(acc, cmul(h[j + q], v[q]));
+                for (int q = 0; q < 4; q++) acc = csub(acc, cmul(h[j + q], v[q]));
+            }
+            for (; j < m; j++) acc = csub(acc, cmul(h[j], d2(Vb[(size_t)j * ldv + i])));
+            w[i] = from_d2<T>(acc);
         }
-        for (; j < m; j++) acc = csub(acc, cmul(h[j], d2(Vb[(size_t)j * ldv + i])));
-        w[i] = from_d2<T>(acc);
     }
 }
 
@@ -135,10 +156,11 @@ __global__ void k_combine(T *__restrict__ out, size_t ldo, const T *__restrict__
 }
 
 // per-block partial sums of |w|^2 (in .x)
-__global__ void k_norm_part(const double2 *__restrict__ w, size_t n, double2 *part) {
+template <typename T>
+__global__ void k_norm_part(const T *__restrict__ w, size_t n, double2 *part) {
     double2 acc = make_double2(0.0, 0.0);
     for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
-        const double2 a = w[i];
+        const double2 a = d2(w[i]);
         acc.x += a.x * a.x + a.y * a.y;
     }
     acc = block_sum2(acc);
@@ -146,8 +168,9 @@ __global__ void k_norm_part(const double2 *__restrict__ w, size_t n, double2 *pa
 }
 
 // v = w / ||w|| (norm from the partials, fixed order); block 0 stores ||w||
-__global__ void k_normalize(double2 *__restrict__ v, const double2 *__restrict__ w, const double2 *__restrict__ part,
-                            int nb, double *nrm_out, size_t n) {
+template <typename T>
+__global__ void k_normalize(T *__restrict__ v, const T *__restrict__ w, const double2 *__restrict__ part, int nb,
+                            double *nrm_out, size_t n) {
     __shared__ double nrm;
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -157,7 +180,8 @@ __global__ void k_normalize(double2 *__restrict__ v, const double2 *__restrict__
     }
     __syncthreads();
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) v[i] = cscale(w[i], inv);
+    for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT)
+        v[i] = from_d2<T>(cscale(d2(w[i]), inv));
 }
 
 // start vector: uniform entries in [-1/2, 1/2) from a counter-based hash (splitmix64)
@@ -167,10 +191,11 @@ BRI_D unsigned long long splitmix64(unsigned long long z) {
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
     return z ^ (z >> 31);
 }
-__global__ void k_rand_vec(double2 *v, size_t n, unsigned long long seed) {
+template <typename T>
+__global__ void k_rand_vec(T *v, size_t n, unsigned long long seed) {
     for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
         const unsigned long long a = splitmix64(seed ^ (2 * i)), b = splitmix64(seed ^ (2 * i + 1));
-        v[i] = make_double2((double)(a >> 11) * 0x1.0p-53 - 0.5, (double)(b >> 11) * 0x1.0p-53 - 0.5);
+        v[i] = from_d2<T>(make_double2((double)(a >> 11) * 0x1.0p-53 - 0.5, (double)(b >> 11) * 0x1.0p-53 - 0.5));
     }
 }
 
@@ -433,12 +458,13 @@ bri_status project_out(bri_ctx *ctx, T *w, const T *Z, int k, double2 *h, cudaSt
 }
 
 // v = w / ||w||; *nrm (device) receives ||w||
-bri_status normalize(bri_ctx *ctx, double2 *v, const double2 *w, double *nrm, cudaStream_t s) {
+template <typename T>
+bri_status normalize(bri_ctx *ctx, T *v, const T *w, double *nrm, cudaStream_t s) {
     OverlapWork *o = ctx->ov;
     BRI_RETURN_IF(ensure_red(ctx, 1));
-    k_norm_part<<<DB, VT, 0, s>>>(w, o->n, o->part);
+    k_norm_part<T><<<DB, VT, 0, s>>>(w, o->n, o->part);
     BRI_LAUNCHED(ctx);
-    k_normalize<<<vec_blocks(o->n), VT, 0, s>>>(v, w, o->part, DB, nrm, o->n);
+    k_normalize<T><<<vec_blocks(o->n), VT, 0, s>>>(v, w, o->part, DB, nrm, o->n);
     BRI_LAUNCHED(ctx);
     return BRI_OK;
 }
@@ -456,7 +482,8 @@ struct LanczosResult {
 // the nlow smallest and the largest Ritz value, converged when every residual
 // estimate is below tol x its Ritz value (tol x the largest for the top).
 // Y (when given) receives the Ritz vectors of the nlow smallest.
-bri_status lanczos(bri_ctx *ctx, double m0, int nlow, int mmax, double tol, const double2 *Z, int nz, double2 *Y,
+template <typename T>
+bri_status lanczos(bri_ctx *ctx, bri_prec aprec, double m0, int nlow, int mmax, double tol, const T *Z, int nz, T *Y,
                    unsigned long long seed, LanczosResult &res, cudaStream_t s) {
     OverlapWork *o = ctx->ov;
     const size_t n = o->n;
@@ -464,44 +491,45 @@ bri_status lanczos(bri_ctx *ctx, double m0, int nlow, int mmax, double tol, cons
     if (nlow + 1 > mmax) return bri_fail(ctx, BRI_EINVAL, "max_krylov must exceed the number of wanted eigenpairs");
     const int nw = nlow + 1;
     DevBuf Vb, wb, tmpb, abb, outb, workb, pwb, Sb;
-    BRI_TRY_CUDA(ctx, cudaMalloc(&Vb.p, sizeof(double2) * n * (size_t)(mmax + 1)));
-    BRI_TRY_CUDA(ctx, cudaMalloc(&wb.p, sizeof(double2) * n));
-    BRI_TRY_CUDA(ctx, cudaMalloc(&tmpb.p, sizeof(double2) * n));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&Vb.p, sizeof(T) * n * (size_t)(mmax + 1)));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&wb.p, sizeof(T) * n));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&tmpb.p, sizeof(T) * n));
     BRI_TRY_CUDA(ctx, cudaMalloc(&abb.p, sizeof(double) * 2 * (size_t)(mmax + 2)));
     BRI_TRY_CUDA(ctx, cudaMalloc(&outb.p, sizeof(double) * 2 * nw));
     BRI_TRY_CUDA(ctx, cudaMalloc(&workb.p, sizeof(double) * 5 * (size_t)mmax * nw));
     BRI_TRY_CUDA(ctx, cudaMalloc(&pwb.p, (size_t)mmax * nw));
     if (nlow > 0 && Y) BRI_TRY_CUDA(ctx, cudaMalloc(&Sb.p, sizeof(double2) * (size_t)mmax * nlow));
-    double2 *V = Vb.as<double2>(), *w = wb.as<double2>(), *tmp = tmpb.as<double2>(), *S = Sb.as<double2>();
+    T *V = Vb.as<T>(), *w = wb.as<T>(), *tmp = tmpb.as<T>();
+    double2 *S = Sb.as<double2>();
     double *ab = abb.as<double>(), *tri_out = outb.as<double>(), *tri_work = workb.as<double>();
     unsigned char *tri_pw = pwb.as<unsigned char>();
     double *alpha = ab, *beta = ab + (mmax + 2);
     BRI_RETURN_IF(ensure_red(ctx, mmax + 1));
     double2 *h = o->h;
     BRI_TRY_CUDA(ctx, cudaMemsetAsync(ab, 0, sizeof(double) * 2 * (size_t)(mmax + 2), s));
-    k_rand_vec<<<vec_blocks(n), VT, 0, s>>>(w, n, seed);
+    k_rand_vec<T><<<vec_blocks(n), VT, 0, s>>>(w, n, seed);
     BRI_LAUNCHED(ctx);
-    BRI_RETURN_IF(project_out<double2>(ctx, w, Z, nz, h, s));
-    BRI_RETURN_IF(project_out<double2>(ctx, w, Z, nz, h, s));
+    BRI_RETURN_IF(project_out<T>(ctx, w, Z, nz, h, s));
+    BRI_RETURN_IF(project_out<T>(ctx, w, Z, nz, h, s));
     BRI_RETURN_IF(normalize(ctx, V, w, beta, s));
     std::vector<double> hout(2 * nw), hab(2 * (size_t)(mmax + 2));
     int m = 0, next_check = std::min(mmax, std::max(nw + 10, 20));
     res = LanczosResult();
     while (m < mmax) {
-        double2 *vj = V + (size_t)m * n;
-        BRI_RETURN_IF(bri_dslash_impl(ctx, tmp, vj, 1, m0, 2, BRI_F64, s));
-        BRI_RETURN_IF(bri_dslash_impl(ctx, w, tmp, 1, m0, 2, BRI_F64, s));
+        T *vj = V + (size_t)m * n;
+        BRI_RETURN_IF(bri_dslash_impl(ctx, tmp, vj, 1, m0, 2, aprec, s));
+        BRI_RETURN_IF(bri_dslash_impl(ctx, w, tmp, 1, m0, 2, aprec, s));
         res.applies += 2;
         // three-term step against v_{j-1}, v_j, then one Gram-Schmidt pass
         // against the whole basis (its coefficients are at rounding level)
         const int j0 = m > 0 ? m - 1 : 0;
-        BRI_RETURN_IF(mdot<double2>(ctx, h, V + (size_t)j0 * n, n, m + 1 - j0, w, alpha + m, s));
-        BRI_RETURN_IF(maxpy<double2>(ctx, w, V + (size_t)j0 * n, n, h, m + 1 - j0, s));
-        BRI_RETURN_IF(mdot<double2>(ctx, h, V, n, m + 1, w, alpha + m, s));
-        BRI_RETURN_IF(maxpy<double2>(ctx, w, V, n, h, m + 1, s));
+        BRI_RETURN_IF(mdot<T>(ctx, h, V + (size_t)j0 * n, n, m + 1 - j0, w, alpha + m, s));
+        BRI_RETURN_IF(maxpy<T>(ctx, w, V + (size_t)j0 * n, n, h, m + 1 - j0, s));
+        BRI_RETURN_IF(mdot<T>(ctx, h, V, n, m + 1, w, alpha + m, s));
+        BRI_RETURN_IF(maxpy<T>(ctx, w, V, n, h, m + 1, s));
         // deflation last: a component along Z left in the new basis vector would
         // grow from step to step (Z is an eigenspace of value 0 of P A P)
-        BRI_RETURN_IF(project_out<double2>(ctx, w, Z, nz, h, s));
+        BRI_RETURN_IF(project_out<T>(ctx, w, Z, nz, h, s));
         BRI_RETURN_IF(normalize(ctx, V + (size_t)(m + 1) * n, w, beta + m + 1, s));
         m++;
         if (m < next_check && m < mmax) continue;
@@ -532,7 +560,7 @@ bri_status lanczos(bri_ctx *ctx, double m0, int nlow, int mmax, double tol, cons
                                 tri_pw);
     BRI_LAUNCHED(ctx);
     if (vectors) {
-        k_combine<double2><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(Y, n, V, n, S, m, m, nlow, n);
+        k_combine<T><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(Y, n, V, n, S, m, m, nlow, n);
         BRI_LAUNCHED(ctx);
     }
     BRI_TRY_CUDA(ctx, cudaMemcpyAsync(hout.data(), tri_out, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, s));
@@ -666,15 +694,110 @@ bri_status sign_one(bri_ctx *ctx, double2 *out, const double2 *in, cudaStream_t 
     return BRI_OK;
 }
 
+struct SetupStats {
+    double lo = 0.0, hi = 0.0, defl_resid = 0.0;
+    int applies = 0, kdim = 0;
+};
+
+// The nlow eigenpairs of H of smallest |lambda| into Z (vectors of type T) and
+// o->lam, and the interval [lo, hi] of the rest of the spectrum of H^2:
+// Lanczos on H^2 for the low modes, Rayleigh-Ritz with H on their Ritz vectors,
+// a second Lanczos on the deflated operator for the interval.  Stencil applies
+// in aprec.
+template <typename T>
+bri_status setup_modes(bri_ctx *ctx, bri_prec aprec, double m0, int nlow, int max_krylov, double tol, T *Z,
+                       SetupStats &st, cudaStream_t s) {
+    OverlapWork *o = ctx->ov;
+    const size_t n = o->n;
+    LanczosResult r1;
+    if (nlow == 0) {
+        BRI_RETURN_IF(lanczos<T>(ctx, aprec, m0, 1, max_krylov, std::max(tol, 1e-4), nullptr, 0, nullptr, 0x3615ull, r1,
+                                 s));
+        st.applies += r1.applies;
+        st.kdim += r1.m;
+        if (!r1.converged) return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: spectral interval of H^2 did not converge");
+        st.lo = (r1.theta[0] - r1.resid[0]) * 0.98;
+        st.hi = (r1.theta[1] + r1.resid[1]) * 1.02;
+        return BRI_OK;
+    }
+    DevBuf Yb, HYb, Mb;
+    BRI_TRY_CUDA(ctx, cudaMalloc(&Yb.p, sizeof(T) * n * nlow));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&HYb.p, sizeof(T) * n * nlow));
+    BRI_TRY_CUDA(ctx, cudaMalloc(&Mb.p, sizeof(double2) * nlow * nlow * 4));
+    T *Y = Yb.as<T>(), *HY = HYb.as<T>();
+    double2 *M = Mb.as<double2>();
+    double2 *Q = M + nlow * nlow, *C = Q + nlow * nlow, *YHY = C + nlow * nlow;
+    BRI_RETURN_IF(lanczos<T>(ctx, aprec, m0, nlow, max_krylov, tol, nullptr, 0, Y, 0x1012ull, r1, s));
+    st.applies += r1.applies;
+    st.kdim += r1.m;
+    if (!r1.converged)
+        return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: low modes of H^2 did not converge; raise max_krylov");
+    // Rayleigh-Ritz of H on the Ritz vectors of H^2
+    for (int b = 0; b < nlow; b++) {
+        BRI_RETURN_IF(bri_dslash_impl(ctx, HY + (size_t)b * n, Y + (size_t)b * n, 1, m0, 2, aprec, s));
+        st.applies++;
+        BRI_RETURN_IF(mdot<T>(ctx, YHY + (size_t)b * nlow, Y, n, nlow, HY + (size_t)b * n, nullptr, s));
+    }
+    k_small_herm<<<1, 32, 0, s>>>(YHY, nlow, M, Q, C, o->lam);
+    BRI_LAUNCHED(ctx);
+    k_combine<T><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(Z, n, Y, n, C, nlow, nlow, nlow, n);
+    BRI_LAUNCHED(ctx);
+    // residuals ||H z - lambda z|| of the deflated pairs
+    std::vector<double> lam(nlow);
+    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(lam.data(), o->lam, sizeof(double) * nlow, cudaMemcpyDeviceToHost, s));
+    BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    std::vector<double2> coefs(nlow), parts(DB);
+    for (int b = 0; b < nlow; b++) coefs[b] = make_double2(lam[b], 0.0);
+    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(o->cdef, coefs.data(), sizeof(double2) * nlow, cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < nlow; b++) {
+        BRI_RETURN_IF(bri_dslash_impl(ctx, HY, Z + (size_t)b * n, 1, m0, 2, aprec, s));
+        st.applies++;
+        BRI_RETURN_IF(maxpy<T>(ctx, HY, Z + (size_t)b * n, n, o->cdef + b, 1, s));
+        k_norm_part<T><<<DB, VT, 0, s>>>(HY, n, o->part);
+        BRI_LAUNCHED(ctx);
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(parts.data(), o->part, sizeof(double2) * DB, cudaMemcpyDeviceToHost, s));
+        BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        double sum = 0.0;
+        for (auto &v : parts) sum += v.x;
+        st.defl_resid = std::max(st.defl_resid, std::sqrt(sum));
+    }
+    o->nlow = nlow;
+    // the rest of the spectrum of H^2: Lanczos on the deflated operator
+    LanczosResult r2;
+    BRI_RETURN_IF(lanczos<T>(ctx, aprec, m0, 1, max_krylov, std::max(tol, 1e-4), Z, nlow, nullptr, 0x3615ull, r2, s));
+    st.applies += r2.applies;
+    st.kdim += r2.m;
+    if (!r2.converged)
+        return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: spectral interval of the deflated H^2 did not converge");
+    st.lo = (r2.theta[0] - r2.resid[0]) * 0.98;
+    st.hi = (r2.theta[1] + r2.resid[1]) * 1.02;
+    return BRI_OK;
+}
+
 }  // namespace
 
 // ---- entry points (argument checks in api.cu) ---------------------------------------
 bri_status bri_eigs_impl(bri_ctx *ctx, double *evals, double *lmax, double *evecs, int nev, double m0, int max_krylov,
-                         double tol, bri_eig_info *info, cudaStream_t s) {
+                         double tol, bri_prec prec, bri_eig_info *info, cudaStream_t s) {
     auto t0 = std::chrono::steady_clock::now();
     BRI_RETURN_IF(ensure_ov(ctx));
     LanczosResult r;
-    BRI_RETURN_IF(lanczos(ctx, m0, nev, max_krylov, tol, nullptr, 0, (double2 *)evecs, 0x1012ull, r, s));
+    if (prec == BRI_F64) {
+        BRI_RETURN_IF(lanczos<double2>(ctx, BRI_F64, m0, nev, max_krylov, tol, nullptr, 0, (double2 *)evecs, 0x1012ull,
+                                       r, s));
+    } else {
+        // FP32 Lanczos (FP32 or FP16 hopping fields): Ritz vectors converted to FP64
+        DevBuf y32;
+        if (evecs) BRI_TRY_CUDA(ctx, cudaMalloc(&y32.p, sizeof(float2) * ctx->ov->n * nev));
+        BRI_RETURN_IF(lanczos<float2>(ctx, prec, m0, nev, max_krylov, tol, nullptr, 0, y32.as<float2>(), 0x1012ull, r,
+                                      s));
+        if (evecs) {
+            k_f32_to_f64<<<vec_blocks(ctx->ov->n * nev), VT, 0, s>>>((double2 *)evecs, y32.as<float2>(),
+                                                                      ctx->ov->n * nev);
+            BRI_LAUNCHED(ctx);
+            BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        }
+    }
     for (int k = 0; k < nev; k++) evals[k] = r.theta[k];
     if (lmax) *lmax = r.theta[nev];
     double mr = 0.0;
@@ -709,81 +832,32 @@ bri_status bri_overlap_setup_impl(bri_ctx *ctx, double rho, int nlow, double eps
     BRI_RETURN_IF(alloc_vecs(ctx, prec));
     BRI_RETURN_IF(ensure_red(ctx, MAX_WANT));
     const double m0 = -rho;
-    int applies = 0, kdim = 0;
-    double defl_resid = 0.0;
-    double lo, hi;
-    LanczosResult r1;
-    if (nlow > 0) {
-        DevBuf Yb, HYb, Mb;
-        BRI_TRY_CUDA(ctx, cudaMalloc(&Yb.p, sizeof(double2) * n * nlow));
-        BRI_TRY_CUDA(ctx, cudaMalloc(&HYb.p, sizeof(double2) * n * nlow));
-        BRI_TRY_CUDA(ctx, cudaMalloc(&Mb.p, sizeof(double2) * nlow * nlow * 4));
-        double2 *Y = Yb.as<double2>(), *HY = HYb.as<double2>(), *M = Mb.as<double2>();
-        double2 *Q = M + nlow * nlow, *C = Q + nlow * nlow, *YHY = C + nlow * nlow;
-        BRI_TRY_CUDA(ctx, cudaMalloc(&o->Z, sizeof(double2) * n * nlow));
-        BRI_TRY_CUDA(ctx, cudaMalloc(&o->lam, sizeof(double) * nlow));
-        BRI_RETURN_IF(lanczos(ctx, m0, nlow, max_krylov, tol, nullptr, 0, Y, 0x1012ull, r1, s));
-        applies += r1.applies;
-        kdim += r1.m;
-        if (!r1.converged)
-            return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: low modes of H^2 did not converge; raise max_krylov");
-        // Rayleigh-Ritz of H on the Ritz vectors of H^2
-        for (int b = 0; b < nlow; b++) {
-            BRI_RETURN_IF(bri_dslash_impl(ctx, HY + (size_t)b * n, Y + (size_t)b * n, 1, m0, 2, BRI_F64, s));
-            applies++;
-            BRI_RETURN_IF(mdot<double2>(ctx, YHY + (size_t)b * nlow, Y, n, nlow, HY + (size_t)b * n, nullptr, s));
-        }
-        k_small_herm<<<1, 32, 0, s>>>(YHY, nlow, M, Q, C, o->lam);
-        BRI_LAUNCHED(ctx);
-        k_combine<double2><<<dim3(vec_blocks(n), (nlow + 3) / 4), VT, 0, s>>>(o->Z, n, Y, n, C, nlow, nlow, nlow, n);
-        BRI_LAUNCHED(ctx);
-        // residuals ||H z - lambda z|| of the deflated pairs
-        std::vector<double> lam(nlow);
-        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(lam.data(), o->lam, sizeof(double) * nlow, cudaMemcpyDeviceToHost, s));
-        BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-        std::vector<double2> coefs(nlow), parts(DB);
-        for (int b = 0; b < nlow; b++) coefs[b] = make_double2(lam[b], 0.0);
-        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(o->cdef, coefs.data(), sizeof(double2) * nlow, cudaMemcpyHostToDevice, s));
-        for (int b = 0; b < nlow; b++) {
-            BRI_RETURN_IF(bri_dslash_impl(ctx, HY, o->Z + (size_t)b * n, 1, m0, 2, BRI_F64, s));
-            applies++;
-            BRI_RETURN_IF(maxpy<double2>(ctx, HY, o->Z + (size_t)b * n, n, o->cdef + b, 1, s));
-            k_norm_part<<<DB, VT, 0, s>>>(HY, n, o->part);
-            BRI_LAUNCHED(ctx);
-            BRI_TRY_CUDA(ctx, cudaMemcpyAsync(parts.data(), o->part, sizeof(double2) * DB, cudaMemcpyDeviceToHost, s));
-            BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-            double sum = 0.0;
-            for (auto &v : parts) sum += v.x;
-            defl_resid = std::max(defl_resid, std::sqrt(sum));
-        }
-        o->nlow = nlow;
-        // the rest of the spectrum of H^2: Lanczos on the deflated operator
-        LanczosResult r2;
-        BRI_RETURN_IF(lanczos(ctx, m0, 1, max_krylov, std::max(tol, 1e-4), o->Z, nlow, nullptr, 0x3615ull, r2, s));
-        applies += r2.applies;
-        kdim += r2.m;
-        if (!r2.converged)
-            return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: spectral interval of the deflated H^2 did not converge");
-        lo = (r2.theta[0] - r2.resid[0]) * 0.98;
-        hi = (r2.theta[1] + r2.resid[1]) * 1.02;
+    SetupStats st;
+    if (nlow > 0) BRI_TRY_CUDA(ctx, cudaMalloc(&o->lam, sizeof(double) * nlow));
+    if (prec == BRI_F64) {
+        if (nlow > 0) BRI_TRY_CUDA(ctx, cudaMalloc(&o->Z, sizeof(double2) * n * nlow));
+        BRI_RETURN_IF(setup_modes<double2>(ctx, BRI_F64, m0, nlow, max_krylov, tol, o->Z, st, s));
     } else {
-        BRI_RETURN_IF(lanczos(ctx, m0, 1, max_krylov, std::max(tol, 1e-4), nullptr, 0, nullptr, 0x3615ull, r1, s));
-        applies += r1.applies;
-        kdim += r1.m;
-        if (!r1.converged) return bri_fail(ctx, BRI_ENOTCONV, "overlap setup: spectral interval of H^2 did not converge");
-        lo = (r1.theta[0] - r1.resid[0]) * 0.98;
-        hi = (r1.theta[1] + r1.resid[1]) * 1.02;
+        // FP32 / FP16 polynomial: the Lanczos runs, the Rayleigh-Ritz step and the
+        // deflation vectors in FP32 too (their accuracy matches the polynomial's);
+        // an FP64 copy of the vectors serves the FP64 deflation of the input
+        if (nlow > 0) {
+            BRI_TRY_CUDA(ctx, cudaMalloc(&o->Z32, sizeof(float2) * n * nlow));
+            BRI_TRY_CUDA(ctx, cudaMalloc(&o->Z, sizeof(double2) * n * nlow));
+        }
+        BRI_RETURN_IF(setup_modes<float2>(ctx, prec, m0, nlow, max_krylov, std::max(tol, 1e-6), o->Z32, st, s));
+        if (nlow > 0) {
+            k_f32_to_f64<<<vec_blocks(n * nlow), VT, 0, s>>>(o->Z, o->Z32, n * nlow);
+            BRI_LAUNCHED(ctx);
+        }
     }
+    const double lo = st.lo, hi = st.hi, defl_resid = st.defl_resid;
+    const int applies = st.applies, kdim = st.kdim;
     if (!(lo > 0.0) || !(hi > lo)) {
         char msg[256];
         snprintf(msg, sizeof msg,
                  "overlap setup: H^2 has a (near) zero mode outside the deflated space (interval [%.3e, %.3e])", lo, hi);
         return bri_fail(ctx, BRI_EINVAL, msg);
-    }
-    if (prec != BRI_F64 && nlow > 0) {
-        BRI_TRY_CUDA(ctx, cudaMalloc(&o->Z32, sizeof(float2) * n * nlow));
-        k_f64_to_f32<<<vec_blocks(n * nlow), VT, 0, s>>>(o->Z32, o->Z, n * nlow);
-        BRI_LAUNCHED(ctx);
     }
     double err = 0.0;
     BRI_RETURN_IF(build_poly(ctx, lo, hi, eps, o->coef, err, s));

@@ -75,8 +75,10 @@ def test_overlap_matches_dense_oracle(gpu, small_case, nlow, prec, tol):
     if nlow:
         lam_ref, _ = ov.kernel_eigenpairs(LS, AP, W, rho)
         lam, _ = op.overlap_modes(nlow)
-        assert np.allclose(lam, lam_ref[:nlow], rtol=1e-8, atol=1e-12)
-        assert info["defl_resid"] < 1e-8
+        # FP32 setups find the modes with FP32 applies: eigenvalues to ~1e-7
+        ltol, rtol = (1e-8, 1e-8) if prec == "f64" else (1e-6, 1e-5)
+        assert np.allclose(lam, lam_ref[:nlow], rtol=ltol, atol=1e-12)
+        assert info["defl_resid"] < rtol
 
 
 def test_ginsparg_wilson_relation_6x6x6x6(gpu):
@@ -117,3 +119,17 @@ def test_free_field_plane_waves_8x8x8x8(gpu):
         got = op.overlap(torch.as_tensor(psi[None], device=gpu)).cpu().numpy()[0]
         want = synth.plane_wave(L, k, Sym @ u)
         assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+
+
+def test_fp32_lanczos_spectrum(gpu, small_case):
+    """FP32 Lanczos (FP32 fields and vectors, FP64 sums): Ritz values to 1e-5."""
+    U, _ = small_case
+    ref = ov.ddag_d_eigenvalues(LS, AP, oracle.build_hops(LS, U), -1.0)
+    op = _op(gpu, LS, U, f32=True)
+    ev, lmax, vecs, info = op.eigs_ddag_d(6, m0=-1.0, max_krylov=1200, tol=1e-6, vectors=True, prec="f32")
+    assert info["status"] == "BRI_OK", info
+    assert np.allclose(ev, ref[:6], rtol=1e-5, atol=0)
+    assert abs(lmax - ref[-1]) <= 1e-5 * ref[-1]
+    y = vecs[0:1]
+    r = op.apply(op.apply(y, -1.0), -1.0, dagger=True) - ev[0] * y
+    assert op.cdot(r, r).real ** 0.5 <= 1e-4 * ref[-1]
