@@ -5,8 +5,9 @@
 // an iteration needs no host round trip: seven launches (p update, apply,
 // <rhat,v> + alpha, s update, apply, <t,s>,<t,t> + omega, x/r update +
 // <rhat,r>,<r,r> + rho).  Each reduction kernel writes per-block FP64 partial
-// sums; the last block to finish (atomic ticket) adds them in block order, so
-// the sums are deterministic, and updates the scalars.  Blocks of iterations
+// sums (a thread's own few elements are summed in the vectors' precision); the
+// last block to finish (atomic ticket) adds them in a fixed order, so the sums
+// are deterministic, and updates the scalars.  Blocks of iterations
 // are captured once into a CUDA graph and replayed; the host reads the
 // convergence flags between replays only.  Converged right-hand sides are
 // skipped by every kernel (flag array), including the stencil apply.
@@ -82,12 +83,20 @@ BRI_D bool partial_and_ticket(double v[NV], double *part, unsigned *ticket) {
     return last;
 }
 
-// in the last block: sum the partials of every block in block order (thread 0)
+// in the last block, all threads: sum the partials of every block (thread t
+// takes blocks t, t + RT, ... in order, then a fixed tree); result in thread 0
 template <int NV> BRI_D void gather_partials(const double *part, double out[NV]) {
     for (int k = 0; k < NV; k++) out[k] = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++)
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RT)
         for (int k = 0; k < NV; k++) out[k] += ((volatile const double *)part)[(size_t)b * NPART + k];
+    block_sum<NV>(out);
 }
+
+// per-thread accumulator of the BiCGstab reductions: FP32 vectors sum their few
+// elements per thread in FP32 (FP64 is 1/64 of the FP32 rate on this GPU),
+// FP64 vectors in FP64; partials across threads and blocks are always FP64
+template <typename T> struct AccT { using A = double; };
+template <> struct AccT<float2> { using A = float; };
 
 BRI_D double2 dcdiv(double2 a, double2 b) {
     double d = b.x * b.x + b.y * b.y;
@@ -116,15 +125,18 @@ __global__ void k_bi_alpha(const T *rhat, const T *v, BiState *st, int *flag, do
     const int rh = blockIdx.y;
     if (flag[rh]) return;
     rhat += rh * n; v += rh * n;
-    double acc[2] = {0, 0};
+    using A = typename AccT<T>::A;
+    A ac[2] = {0, 0};
     for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
         T a = rhat[i], b = v[i];
-        acc[0] += (double)a.x * b.x + (double)a.y * b.y;
-        acc[1] += (double)a.x * b.y - (double)a.y * b.x;
+        ac[0] += (A)a.x * b.x + (A)a.y * b.y;
+        ac[1] += (A)a.x * b.y - (A)a.y * b.x;
     }
-    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh) && threadIdx.x == 0) {
+    double acc[2] = {ac[0], ac[1]};
+    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh)) {
         double s[2];
         gather_partials<2>(part + (size_t)rh * RBLK * NPART, s);
+        if (threadIdx.x != 0) return;
         double2 rv = make_double2(s[0], s[1]);
         if (!finite2(rv)) flag[rh] = 3;
         else if (rv.x == 0.0 && rv.y == 0.0) flag[rh] = 2;
@@ -148,16 +160,19 @@ __global__ void k_bi_omega(const T *t, const T *s, BiState *st, int *flag, doubl
     const int rh = blockIdx.y;
     if (flag[rh]) return;
     t += rh * n; s += rh * n;
-    double acc[3] = {0, 0, 0};
+    using A = typename AccT<T>::A;
+    A ac[3] = {0, 0, 0};
     for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
         T a = t[i], b = s[i];
-        acc[0] += (double)a.x * b.x + (double)a.y * b.y;
-        acc[1] += (double)a.x * b.y - (double)a.y * b.x;
-        acc[2] += (double)a.x * a.x + (double)a.y * a.y;
+        ac[0] += (A)a.x * b.x + (A)a.y * b.y;
+        ac[1] += (A)a.x * b.y - (A)a.y * b.x;
+        ac[2] += (A)a.x * a.x + (A)a.y * a.y;
     }
-    if (partial_and_ticket<3>(acc, part + (size_t)rh * RBLK * NPART, tick + rh) && threadIdx.x == 0) {
+    double acc[3] = {ac[0], ac[1], ac[2]};
+    if (partial_and_ticket<3>(acc, part + (size_t)rh * RBLK * NPART, tick + rh)) {
         double q[3];
         gather_partials<3>(part + (size_t)rh * RBLK * NPART, q);
+        if (threadIdx.x != 0) return;
         if (!isfinite(q[0]) || !isfinite(q[1]) || !isfinite(q[2])) flag[rh] = 3;
         else if (q[2] == 0.0) flag[rh] = 2;
         else st[rh].omega = make_double2(q[0] / q[2], q[1] / q[2]);
@@ -172,20 +187,23 @@ __global__ void k_bi_xr(T *x, T *r, const T *p, const T *s, const T *t, const T 
     if (flag[rh]) return;
     const T a = tc<T>(st[rh].alpha), om = tc<T>(st[rh].omega);
     const size_t o = rh * n;
-    double acc[3] = {0, 0, 0};
+    using A = typename AccT<T>::A;
+    A ac[3] = {0, 0, 0};
     for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
         T si = s[o + i];
         x[o + i] = cadd(x[o + i], cadd(cmul(a, p[o + i]), cmul(om, si)));
         T ri = csub(si, cmul(om, t[o + i]));
         r[o + i] = ri;
         T h = rhat[o + i];
-        acc[0] += (double)h.x * ri.x + (double)h.y * ri.y;
-        acc[1] += (double)h.x * ri.y - (double)h.y * ri.x;
-        acc[2] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+        ac[0] += (A)h.x * ri.x + (A)h.y * ri.y;
+        ac[1] += (A)h.x * ri.y - (A)h.y * ri.x;
+        ac[2] += (A)ri.x * ri.x + (A)ri.y * ri.y;
     }
-    if (partial_and_ticket<3>(acc, part + (size_t)rh * RBLK * NPART, tick + rh) && threadIdx.x == 0) {
+    double acc[3] = {ac[0], ac[1], ac[2]};
+    if (partial_and_ticket<3>(acc, part + (size_t)rh * RBLK * NPART, tick + rh)) {
         double q[3];
         gather_partials<3>(part + (size_t)rh * RBLK * NPART, q);
+        if (threadIdx.x != 0) return;
         BiState &S = st[rh];
         S.iters++;
         S.rho_old = S.rho;
@@ -205,7 +223,8 @@ __global__ void k_bi_init(T *r, T *rhat, T *p, T *v, const T *b, int have_ax, Bi
                           int maxit, double *part, unsigned *tick, size_t n) {
     const int rh = blockIdx.y;
     const size_t o = rh * n;
-    double acc[2] = {0, 0};
+    using A = typename AccT<T>::A;
+    A ac[2] = {0, 0};
     for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
         T bi = b[o + i];
         T ri = have_ax ? csub(bi, r[o + i]) : bi;
@@ -213,12 +232,14 @@ __global__ void k_bi_init(T *r, T *rhat, T *p, T *v, const T *b, int have_ax, Bi
         rhat[o + i] = ri;
         p[o + i] = mk<T>(0, 0);
         v[o + i] = mk<T>(0, 0);
-        acc[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
-        acc[1] += (double)bi.x * bi.x + (double)bi.y * bi.y;
+        ac[0] += (A)ri.x * ri.x + (A)ri.y * ri.y;
+        ac[1] += (A)bi.x * bi.x + (A)bi.y * bi.y;
     }
-    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh) && threadIdx.x == 0) {
+    double acc[2] = {ac[0], ac[1]};
+    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh)) {
         double q[2];
         gather_partials<2>(part + (size_t)rh * RBLK * NPART, q);
+        if (threadIdx.x != 0) return;
         BiState S;
         S.rho = make_double2(q[0], 0.0);
         S.rho_old = S.alpha = S.omega = make_double2(1.0, 0.0);
@@ -246,9 +267,10 @@ __global__ void k_residual64(double2 *ax, const double2 *b, double *nrm, double 
         acc[0] += ri.x * ri.x + ri.y * ri.y;
         acc[1] += bi.x * bi.x + bi.y * bi.y;
     }
-    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh) && threadIdx.x == 0) {
+    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh)) {
         double q[2];
         gather_partials<2>(part + (size_t)rh * RBLK * NPART, q);
+        if (threadIdx.x != 0) return;
         nrm[2 * rh] = q[0];
         nrm[2 * rh + 1] = q[1];
         tick[rh] = 0;
@@ -286,9 +308,10 @@ __global__ void k_cdot(const T *a, const T *b, size_t n, double *out, double *pa
         acc[0] += (double)x.x * y.x + (double)x.y * y.y;
         acc[1] += (double)x.x * y.y - (double)x.y * y.x;
     }
-    if (partial_and_ticket<2>(acc, part, tick) && threadIdx.x == 0) {
+    if (partial_and_ticket<2>(acc, part, tick)) {
         double q[2];
         gather_partials<2>(part, q);
+        if (threadIdx.x != 0) return;
         out[0] = q[0];
         out[1] = q[1];
         tick[0] = 0;
