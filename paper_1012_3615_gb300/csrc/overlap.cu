@@ -311,14 +311,16 @@ __global__ void k_cheb_err(const double *__restrict__ c, int N, double lo, doubl
 template <typename T>
 __global__ void k_cheb_step(T *out, const T *__restrict__ v, const T *__restrict__ Bb, const T *__restrict__ b1,
                             const T *b2, double ck, double s2, double t2, int have_b1, int have_b2, size_t n) {
+    using R = decltype(T().x);  // arithmetic in the vectors' precision
+    const R c = (R)ck, s = (R)s2, t = (R)t2;
     for (size_t i = (size_t)blockIdx.x * VT + threadIdx.x; i < n; i += (size_t)gridDim.x * VT) {
-        double2 r = cscale(d2(v[i]), ck);
+        T r = cscale(v[i], c);
         if (have_b1) {
-            r = cadd(r, cscale(d2(Bb[i]), s2));
-            r = csub(r, cscale(d2(b1[i]), t2));
+            r = cadd(r, cscale(Bb[i], s));
+            r = csub(r, cscale(b1[i], t));
         }
-        if (have_b2) r = csub(r, d2(b2[i]));
-        out[i] = from_d2<T>(r);
+        if (have_b2) r = csub(r, b2[i]);
+        out[i] = r;
     }
 }
 
