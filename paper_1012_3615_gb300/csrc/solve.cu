@@ -276,6 +276,23 @@ __global__ void k_residual64(double2 *ax, const double2 *b, double *nrm, double 
         tick[rh] = 0;
     }
 }
+// ||x||^2 per right-hand side into nrm[2*rh] (is the initial guess zero?)
+__global__ void k_norm64(const double2 *x, double *nrm, double *part, unsigned *tick, size_t n) {
+    const int rh = blockIdx.y;
+    const size_t o = rh * n;
+    double acc[2] = {0, 0};
+    for (size_t i = (size_t)blockIdx.x * RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
+        double2 v = x[o + i];
+        acc[0] += v.x * v.x + v.y * v.y;
+    }
+    if (partial_and_ticket<2>(acc, part + (size_t)rh * RBLK * NPART, tick + rh)) {
+        double q[2];
+        gather_partials<2>(part + (size_t)rh * RBLK * NPART, q);
+        if (threadIdx.x != 0) return;
+        nrm[2 * rh] = q[0];
+        tick[rh] = 0;
+    }
+}
 // out32 = r64 / ||r64||
 // (finished right-hand sides get a zero source, which BiCGstab flags as converged at once)
 __global__ void k_to32(float2 *out, const double2 *in, const double *nrm, const int *done, size_t n) {
@@ -493,10 +510,17 @@ bri_status bicgstab(bri_ctx *ctx, const VecSet &vs, const T *b, bool have_x0, in
 }
 
 // FP64 true residual of (x, b): nrm[2r] = ||b - Dx||^2, nrm[2r+1] = ||b||^2, r64 holds b - Dx
+// r64 = b - D x and the norms ||r||^2, ||b||^2 (host nrm).  x_zero: the guess is
+// zero for every RHS, so D x = 0 needs no apply; skip (device, optional): RHS
+// whose residual is not needed
 bri_status true_residual(bri_ctx *ctx, const double2 *x, const double2 *b, double2 *r64, int nrhs, double m0,
-                         cudaStream_t s, std::vector<double> &nrm) {
+                         cudaStream_t s, std::vector<double> &nrm, bool x_zero = false, const int *skip = nullptr) {
     SolverWork *w = ctx->work;
-    BRI_RETURN_IF(bri_dslash_raw(ctx, r64, x, nrhs, m0, 0, BRI_F64, nullptr, bri_dslash_threads(ctx, BRI_F64, nrhs), s));
+    if (x_zero)
+        BRI_TRY_CUDA(ctx, cudaMemsetAsync(r64, 0, sizeof(double2) * w->n * nrhs, s));
+    else
+        BRI_RETURN_IF(
+            bri_dslash_raw(ctx, r64, x, nrhs, m0, 0, BRI_F64, skip, bri_dslash_threads(ctx, BRI_F64, nrhs), s));
     k_residual64<<<dim3(RBLK, nrhs), RT, 0, s>>>(r64, b, w->nrm, w->part, w->tick, w->n);
     BRI_LAUNCHED(ctx);
     nrm.resize(2 * nrhs);
@@ -552,8 +576,21 @@ bri_status solve_mixed(bri_ctx *ctx, double2 *x, const double2 *b, int nrhs, dou
     std::vector<int> done(nrhs, 0), flags, iters, tot(nrhs, 0), outer(nrhs, 0);
     std::vector<double> nrm, rel(nrhs, 0.0);
     std::vector<bri_status> sts(nrhs, BRI_ENOTCONV);
+    // a zero initial guess (the usual case) needs no FP64 apply for r = b
+    bool x_zero = true;
+    {
+        k_norm64<<<dim3(RBLK, nrhs), RT, 0, s>>>(x, w->nrm, w->part, w->tick, n);
+        BRI_LAUNCHED(ctx);
+        std::vector<double> xn(2 * nrhs);
+        BRI_TRY_CUDA(ctx, cudaMemcpyAsync(xn.data(), w->nrm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s));
+        BRI_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        for (int r = 0; r < nrhs; r++)
+            if (xn[2 * r] != 0.0) x_zero = false;
+    }
+    BRI_TRY_CUDA(ctx, cudaMemcpyAsync(w->done, done.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
     for (int cyc = 0; cyc < 200; cyc++) {
-        BRI_RETURN_IF(true_residual(ctx, x, b, w->r64, nrhs, m0, s, nrm));
+        // converged right-hand sides (device flags of the previous cycle) are skipped
+        BRI_RETURN_IF(true_residual(ctx, x, b, w->r64, nrhs, m0, s, nrm, cyc == 0 && x_zero, w->done));
         bool all = true;
         for (int r = 0; r < nrhs; r++) {
             if (done[r]) continue;
