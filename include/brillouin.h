@@ -343,9 +343,13 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * the cp.async shared-memory link-prefetch variant (at most 256 threads),
  * adding 6144 the site-pair kernel (two sites per thread, full and 2-row
  * storage with an even t extent; otherwise the plain kernel), adding 8192 the
- * plain kernel without the separate accumulator for the +-i gamma entries.
- * bri_get_threads returns the current choice (untuned: 128 for BRI_F64,
- * 128 + 2048 otherwise) or a negative bri_status. */
+ * plain kernel without the separate accumulator for the +-i gamma entries,
+ * adding 10240 the L2 link-prefetch kernel that combines the hops d and -d
+ * before their gamma terms, adding 12288 that kernel held to 128 registers.
+ * bri_get_threads returns the current choice or a negative bri_status;
+ * untuned, 128 threads with: the unrolled kernel (BRI_F64); variant 10240
+ * (FP32 full, FP16 2-row fields); 12288 (FP32 2-row, 8-parameter fields);
+ * 2048 (FP16 full fields). */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 

@@ -133,6 +133,7 @@ struct HopArg {
     int j;
     int hd;
     float lam, rho;
+    float fd[4];  // d_mu as floats (no conversions in the hop loop)
 };
 
 // Lattice geometry and the class weights of the operator (lambda_0..4,
@@ -171,7 +172,10 @@ inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) 
         const int k = canon_k(j), n = off_class(k);
         if (g.lamd[n] == 0.0 && g.rhod[n] == 0.0) continue;
         HopArg &h = g.hop[g.nhop++];
-        for (int mu = 0; mu < 4; mu++) h.dm[mu] = off_comp(k, mu);
+        for (int mu = 0; mu < 4; mu++) {
+            h.dm[mu] = off_comp(k, mu);
+            h.fd[mu] = (float)h.dm[mu];
+        }
         h.j = j;
         h.hd = h.dm[0] + (TX + 2) * (h.dm[1] + (TY + 2) * (h.dm[2] + (TZ + 2) * h.dm[3]));
         h.lam = g.lam[n];

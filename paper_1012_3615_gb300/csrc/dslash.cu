@@ -26,14 +26,26 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
     return buf;
 }
 
+// Untuned launch shape per storage format, 128 threads each: FP64 -> unrolled
+// kernel; otherwise the hop-pair loop with L2 link prefetch in the form that
+// was fastest on 32^3x64 for 1-24 right-hand sides: (d, -d) combined before
+// the gamma terms (variant 5) for FP32 full and FP16 2-row fields, the same
+// held to 128 registers (variant 6) for the 2-row FP32 and 8-parameter
+// fields, one hop at a time (variant 1) for FP16 full fields.
+static int default_shape(bri_ctx *ctx, bri_prec prec) {
+    if (prec == BRI_F64) return 128;
+    const bri_comp c = (prec == BRI_F32 ? ctx->f32 : ctx->f16).comp;
+    if (c == BRI_LINK_8PARAM) return 128 | (6 << 11);
+    if (prec == BRI_F32) return c == BRI_LINK_FULL ? 128 | (5 << 11) : 128 | (6 << 11);
+    return c == BRI_LINK_FULL ? 128 | (1 << 11) : 128 | (5 << 11);
+}
+
 // launch shape (threads per block, kernel variant in bits 11+; see
-// bri_set_threads).  Untuned default: FP64 -> unrolled kernel, 128 threads;
-// FP32 arithmetic -> hop loop with L2 link prefetch, 128 threads (the fastest
-// shape measured on 32^3x64 and 16^3x32).
+// bri_set_threads): the tuned one for (lattice, prec, storage, nrhs) if any
 int bri_dslash_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
     auto it = ctx->tune.find(bri_tune_key(ctx, prec, nrhs));
     if (it != ctx->tune.end()) return it->second;
-    return prec == BRI_F64 ? 128 : (128 | 2048);
+    return default_shape(ctx, prec);
 }
 
 static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void *in, int nrhs, double m0, int mode,
@@ -52,7 +64,7 @@ bri_status bri_dslash_range(bri_ctx *ctx, void *out, const void *in, int nrhs, d
     g.s0 = s0;
     g.s1 = s1;
     int threads = bri_dslash_threads(ctx, prec, nrhs);
-    if ((threads & 2047) == 0 || (threads >> 11) == 3) threads = prec == BRI_F64 ? 128 : (128 | 2048);
+    if ((threads & 2047) == 0 || (threads >> 11) == 3) threads = default_shape(ctx, prec);
     return dslash_geom(ctx, g, out, in, nrhs, m0, mode, prec, nullptr, threads, s);
 }
 

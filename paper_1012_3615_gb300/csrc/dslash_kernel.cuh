@@ -214,6 +214,85 @@ BRI_D void hop_body_w(const M3<float2> &W, const float2 p[12], float l, float r,
     }
 }
 
+// chi = W psi (SGN = 1) or W^dagger psi (SGN = -1) for the four spins, with
+// packed FMAs as in hop_body
+template <int SGN>
+BRI_D void colour_mv(const M3<float2> &W, const float2 p[12], float2 chi[12]) {
+    float2 A[9], B[9];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) {
+            const float2 w = SGN > 0 ? W.e[3 * c + cp] : make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
+            A[3 * c + cp] = w;
+            B[3 * c + cp] = make_float2(-w.y, w.x);
+        }
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
+            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
+            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
+            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
+            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
+            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
+            chi[3 * sp + c] = t;
+        }
+}
+
+// One (d, -d) pair at once.  With q = phf phb (boundary phases, +-1) the two
+// hops add up to
+//   phf [ lam (chi_f + q chi_b) + rsign rho sum_mu d_mu gamma_mu (chi_f - q chi_b) ],
+// chi_f = W_d(x) psi(x + d), chi_b = W_d(x - d)^dagger psi(x - d): the gamma
+// terms are taken once per pair on the difference instead of once per hop, which
+// saves 12 (n - 1) packed FMAs per pair of class n.  cf holds chi_f; W and p are
+// the reversed hop's field and spinor; L = lam phf, R = rsign rho phf.
+BRI_D void pair_body(const float2 cf[12], const M3<float2> &W, const float2 p[12], float L, float q, float R,
+                     const HopArg &h, AccF &acc) {
+    float2 A[9], B[9];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) {
+            const float2 w = make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
+            A[3 * c + cp] = w;
+            B[3 * c + cp] = make_float2(-w.y, w.x);
+        }
+    float rd[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) rd[mu] = R * h.fd[mu];
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        float2 sm[3], df[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
+            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
+            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
+            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
+            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
+            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
+            sm[c] = __ffma2_rn(f2(q), t, cf[3 * sp + c]);
+            df[c] = __ffma2_rn(f2(-q), t, cf[3 * sp + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc.a[3 * sp + c] = __ffma2_rn(f2(L), sm[c], acc.a[3 * sp + c]);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            if (h.dm[mu] == 0) continue;  // uniform across the warp
+            const int s = gcol(mu, sp);
+            const int gr = gre(mu, s), gi = gim(mu, s);
+            const float cfm = gr != 0 ? (gr > 0 ? rd[mu] : -rd[mu]) : (gi > 0 ? rd[mu] : -rd[mu]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cfm), df[c], acc.a[3 * s + c]);
+                else acc.ai[3 * s + c] = __ffma2_rn(f2(cfm), df[c], acc.ai[3 * s + c]);
+            }
+        }
+    }
+}
+
 // neighbour index and boundary phase of the forward (d) and reversed (-d) hop
 BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &phf, int &yb, float &phb) {
     yf = yb = site;
@@ -231,7 +310,35 @@ BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &p
 template <bool PF, int BODY, class LL>
 BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
                     const Geom &g, AccF &acc) {
-    if constexpr (!PF && BODY == 1) {
+    if constexpr (BODY == 2) {
+        // pair-combined body (pair_body), links of the next pair prefetched into L2
+#pragma unroll 1
+        for (int t = 0; t < g.nhop; t++) {
+            if (PF && t + 1 < g.nhop) {
+                const HopArg hp = g.hop[t + 1];
+                int pyf, pyb;
+                float pphf, pphb;
+                hop_nb(hp.dm, site, nb, pyf, pphf, pyb, pphb);
+                ll.prefetch_field_l2(hp.j, site);
+                ll.prefetch_field_l2(hp.j, pyb);
+            }
+            const HopArg hc = g.hop[t];
+            int yf, yb;
+            float phf, phb;
+            hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+            float2 cf[12];
+            {
+                M3<float2> W = ll.load(hc.j, site);
+                float2 q[12];
+                load_spinor(in + (size_t)yf * 12, q);
+                colour_mv<1>(W, q, cf);
+            }
+            M3<float2> W = ll.load(hc.j, yb);
+            float2 q[12];
+            load_spinor(in + (size_t)yb * 12, q);
+            pair_body(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+        }
+    } else if constexpr (!PF && BODY == 1) {
 #pragma unroll 1
         for (int t = 0; t < g.nhop; t++) {
             const HopArg hc = g.hop[t];
@@ -489,9 +596,9 @@ BRI_D void clover_add(const Geom &g, int site, const T p[12], T o[12]) {
 
 // CLOV: add the clover term of Geom in the epilogue (a separate instantiation,
 // so that the kernels without it keep their register budget)
-template <class LL, int VAR, bool CLOV = false>
-__global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out, Geom g,
-                         double diag, const int *__restrict__ skip) {
+template <class LL, int VAR, bool CLOV>
+BRI_D void dslash_body(int mode, const LL &ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out,
+                       const Geom &g, double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
     using R = typename RealOf<T>::R;
     // grid.x = site blocks x right-hand sides with the RHS fastest, so the blocks
@@ -522,7 +629,7 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
             const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 16u;
             f32_hops_cpasync(ll, in, site, nb, rsign, g, lbase, acc);
         } else {
-            f32_hops<VAR == 1, VAR == 4 ? 1 : 0>(ll, in, site, nb, rsign, g, acc);
+            f32_hops<VAR == 1 || VAR == 5, VAR == 4 ? 1 : VAR == 5 ? 2 : 0>(ll, in, site, nb, rsign, g, acc);
         }
     } else {
         all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, g, acc);
@@ -548,6 +655,19 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
         for (int i = 6; i < 12; i++) { o[i].x = -o[i].x; o[i].y = -o[i].y; }
     }
     store_spinor(out + (size_t)site * 12, o);
+}
+
+template <class LL, int VAR, bool CLOV = false>
+__global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out,
+                         Geom g, double diag, const int *__restrict__ skip) {
+    dslash_body<LL, VAR, CLOV>(mode, ll, in, out, g, diag, skip);
+}
+// launch variant 6: the variant-5 loop held to 128 registers (16 warps per SM)
+template <class LL>
+__global__ void __maxnreg__(128) k_dslash_r128(int mode, LL ll, const typename LL::T *__restrict__ in,
+                                               typename LL::T *__restrict__ out, Geom g, double diag,
+                                               const int *__restrict__ skip) {
+    dslash_body<LL, 5, false>(mode, ll, in, out, g, diag, skip);
 }
 
 // ---- shared-memory tiled variant (FP32 spinors) ------------------------------
@@ -694,7 +814,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         }
     }
     if (g.clov64) {  // clover term on: the plain kernel (link prefetch variant for FP32) with the term
-        constexpr int VC = sizeof(T) == 8 ? 1 : 0;
+        constexpr int VC = sizeof(T) == 8 ? 5 : 0;
         static int max_c = 0;
         if (max_c == 0) {
             cudaFuncAttributes attr;
@@ -724,15 +844,17 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     const int variant = threads >> 11;
     threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads[5] = {0, 0, 0, 0, 0};  // per-kernel limit from its register use
+    static int max_threads[7] = {0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
-        const int v = (variant == 1 || variant == 2 || variant == 4) ? variant : 0;
+        const int v = (variant == 1 || variant == 2 || variant >= 4) ? variant : 0;
         if (max_threads[v] == 0) {
             cudaFuncAttributes attr;
             cudaError_t e = v == 1 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 1>)
                           : v == 2 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 2>)
                           : v == 4 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 4>)
+                          : v == 5 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 5>)
+                          : v == 6 ? cudaFuncGetAttributes(&attr, k_dslash_r128<LL>)
                                    : cudaFuncGetAttributes(&attr, k_dslash<LL, 0>);
             max_threads[v] = e == cudaSuccess ? attr.maxThreadsPerBlock : 128;
             if (v == 2) {
@@ -746,6 +868,8 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads) * (unsigned)nrhs);
         if (v == 1) k_dslash<LL, 1><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 4) k_dslash<LL, 4><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else if (v == 5) k_dslash<LL, 5><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else if (v == 6) k_dslash_r128<LL><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 2)
             k_dslash<LL, 2><<<grid, threads, threads * 4 * LL::SLOTS * 16, s>>>(mode, ll, (const T *)in, (T *)out, g,
                                                                                  diag, skip);

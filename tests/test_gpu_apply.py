@@ -7,6 +7,7 @@ import torch
 
 import oracle
 from paper_1012_3615_gb300 import Brillouin, BriError, synth
+from paper_1012_3615_gb300.core import WEIGHTS
 
 pytestmark = pytest.mark.gpu
 AP = (1, 1, 1, -1)
@@ -100,7 +101,7 @@ def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
 def test_kernel_variants_agree(gpu, prec, comp):
     """Every launch shape of the FP32-arithmetic stencil (plain kernel at several
     block sizes, register link prefetch, cp.async link prefetch, fewer-register
-    form) computes the same result to FP32 rounding."""
+    form, (d, -d) pair-combined form) computes the same result to FP32 rounding."""
     L, bc = (6, 5, 4, 8), AP
     U = synth.random_su3_links(L, 0.4, 41)
     psi = synth.gaussian_spinor(L, 2, 42).astype(np.complex64)
@@ -108,7 +109,8 @@ def test_kernel_variants_agree(gpu, prec, comp):
     op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
     x = torch.as_tensor(psi, device=gpu)
     outs = []
-    for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256, 8192 + 128, 8192 + 256):
+    for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256, 8192 + 128, 8192 + 256,
+                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128):
         op.set_threads(prec, 2, shape)
         outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
     for shape, o in outs[1:]:
@@ -135,6 +137,36 @@ def test_pair_kernel_matches_oracle(gpu, prec, comp, tol, L, bc):
             assert _rel_l2(out[r], oracle.apply(L, bc, W, 0.05, psi[r])) < tol
             assert _rel_l2(outd[r], oracle.apply(L, bc, W, 0.05, psi[r], dagger=True)) < tol
             assert _rel_l2(outh[r], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) < tol
+
+
+@pytest.mark.parametrize("prec,comp,tol", [("f32", "full", 1e-6), ("f32", "8param", 1e-6), ("f16", "2row", 2e-3)])
+@pytest.mark.parametrize("L,bc", [((3, 5, 4, 6), AP), ((4, 4, 4, 4), PER)])
+def test_pair_combined_body_matches_oracle(gpu, prec, comp, tol, L, bc):
+    """The loop that combines the hops d and -d before the gamma terms (launch
+    variants 5 and 6) against the oracle for D, D^dagger and the overlap kernel, with
+    the Brillouin and the Wilson weights."""
+    U, psi, W = _setup(L, bc, 60 + sum(L))
+    for name in ("brillouin", "wilson"):
+        lam, rho = WEIGHTS[name]
+        op = Brillouin(L, bc)
+        op.set_weights(lam, rho)
+        op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+        x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
+        oracle.set_weights(lam, rho)
+        try:
+            ref = [(oracle.apply(L, bc, W, 0.05, psi[r]), oracle.apply(L, bc, W, 0.05, psi[r], dagger=True),
+                    oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) for r in range(psi.shape[0])]
+        finally:
+            oracle.reset_weights()
+        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128):
+            op.set_threads(prec, 2, shape)
+            out = op.apply(x, m0=0.05, prec=prec).cpu().numpy()
+            outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
+            outh = op.overlap_kernel(x, rho=1.0, prec=prec).cpu().numpy()
+            for r in range(psi.shape[0]):
+                assert _rel_l2(out[r], ref[r][0]) < tol, (shape, name)
+                assert _rel_l2(outd[r], ref[r][1]) < tol, (shape, name)
+                assert _rel_l2(outh[r], ref[r][2]) < tol, (shape, name)
 
 
 def test_multi_rhs_equals_single(gpu):
