@@ -345,11 +345,12 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * storage with an even t extent; otherwise the plain kernel), adding 8192 the
  * plain kernel without the separate accumulator for the +-i gamma entries,
  * adding 10240 the L2 link-prefetch kernel that combines the hops d and -d
- * before their gamma terms, adding 12288 that kernel held to 128 registers.
+ * before their gamma terms, adding 12288 that kernel held to 128 registers,
+ * adding 14336 the same pair loop with the gamma terms after the spin loop.
  * bri_get_threads returns the current choice or a negative bri_status;
  * untuned, 128 threads with: the unrolled kernel (BRI_F64); variant 10240
- * (FP32 full, FP16 2-row fields); 12288 (FP32 2-row, 8-parameter fields);
- * 2048 (FP16 full fields). */
+ * (FP32 full, FP16 2-row fields); 14336 (FP32 2-row, FP16 full fields);
+ * 12288 (8-parameter fields). */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 

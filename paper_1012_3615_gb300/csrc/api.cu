@@ -378,7 +378,7 @@ bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_prec(ctx, prec));
     const int thr = threads & 2047, variant = threads >> 11;
-    if (nrhs < 1 || threads < 0 || (thr > 0 && thr < 32) || thr > 1024 || variant > 6)
+    if (nrhs < 1 || threads < 0 || (thr > 0 && thr < 32) || thr > 1024 || variant > 7)
         return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
     ctx->tune[bri_tune_key(ctx, prec, nrhs)] = (thr & ~31) | (variant << 11);
     return BRI_OK;
@@ -414,7 +414,7 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     // candidates: tiled kernel (0), plain kernel at 64..512 threads, and the
     // variants of the FP32 plain kernel (launch shape above bit 11)
     for (int thr : {0, 64, 128, 256, 512, 128 | 2048, 128 | 4096, 256 | 4096, 64 | 6144, 128 | 6144, 128 | 8192,
-                    256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288}) {
+                    256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288, 128 | 14336}) {
         if (thr == 0 && (prec == BRI_F64 || !tiled_ok(ctx->g))) continue;
         if ((thr >> 11) && prec == BRI_F64) continue;
         if ((st = bri_dslash_raw(ctx, out, in, nrhs, 0.0, 0, prec, nullptr, thr, s)) != BRI_OK) break;  // warm-up

@@ -246,9 +246,64 @@ BRI_D void colour_mv(const M3<float2> &W, const float2 p[12], float2 chi[12]) {
 //   phf [ lam (chi_f + q chi_b) + rsign rho sum_mu d_mu gamma_mu (chi_f - q chi_b) ],
 // chi_f = W_d(x) psi(x + d), chi_b = W_d(x - d)^dagger psi(x - d): the gamma
 // terms are taken once per pair on the difference instead of once per hop, which
+// saves 12 (n - 1) packed FMAs per pair of class n.  cf holds chi_f on entry and
+// is overwritten with the difference, so the gamma terms run after the spin
+// loop with one warp-uniform branch per direction.  W and p are the reversed
+// hop's field and spinor; L = lam phf, R = rsign rho phf.
+BRI_D void pair_body(float2 cf[12], const M3<float2> &W, const float2 p[12], float L, float q, float R,
+                     const HopArg &h, AccF &acc) {
+    float2 A[9], B[9];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) {
+            const float2 w = make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
+            A[3 * c + cp] = w;
+            B[3 * c + cp] = make_float2(-w.y, w.x);
+        }
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
+            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
+            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
+            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
+            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
+            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
+            const float2 sm = __ffma2_rn(f2(q), t, cf[3 * sp + c]);
+            cf[3 * sp + c] = __ffma2_rn(f2(-q), t, cf[3 * sp + c]);
+            acc.a[3 * sp + c] = __ffma2_rn(f2(L), sm, acc.a[3 * sp + c]);
+        }
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (h.dm[mu] == 0) continue;  // uniform across the warp
+        const float rd = R * h.fd[mu];
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) {
+            const int s = gcol(mu, sp);
+            const int gr = gre(mu, s), gi = gim(mu, s);
+            const float cfm = gr != 0 ? (gr > 0 ? rd : -rd) : (gi > 0 ? rd : -rd);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(cfm), cf[3 * sp + c], acc.a[3 * s + c]);
+                else acc.ai[3 * s + c] = __ffma2_rn(f2(cfm), cf[3 * sp + c], acc.ai[3 * s + c]);
+            }
+        }
+    }
+}
+
+// One (d, -d) pair at once with the gamma terms inside the spin loop (launch
+// variants 5 and 6; pair_body below is the same arithmetic with the gamma
+// terms after the spin loop, variant 7).  With q = phf phb (boundary phases, +-1) the two
+// hops add up to
+//   phf [ lam (chi_f + q chi_b) + rsign rho sum_mu d_mu gamma_mu (chi_f - q chi_b) ],
+// chi_f = W_d(x) psi(x + d), chi_b = W_d(x - d)^dagger psi(x - d): the gamma
+// terms are taken once per pair on the difference instead of once per hop, which
 // saves 12 (n - 1) packed FMAs per pair of class n.  cf holds chi_f; W and p are
 // the reversed hop's field and spinor; L = lam phf, R = rsign rho phf.
-BRI_D void pair_body(const float2 cf[12], const M3<float2> &W, const float2 p[12], float L, float q, float R,
+BRI_D void pair_body_s(const float2 cf[12], const M3<float2> &W, const float2 p[12], float L, float q, float R,
                      const HopArg &h, AccF &acc) {
     float2 A[9], B[9];
 #pragma unroll
@@ -310,7 +365,7 @@ BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &p
 template <bool PF, int BODY, class LL>
 BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
                     const Geom &g, AccF &acc) {
-    if constexpr (BODY == 2) {
+    if constexpr (BODY == 2 || BODY == 3) {
         // pair-combined body (pair_body), links of the next pair prefetched into L2
 #pragma unroll 1
         for (int t = 0; t < g.nhop; t++) {
@@ -336,7 +391,8 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
             M3<float2> W = ll.load(hc.j, yb);
             float2 q[12];
             load_spinor(in + (size_t)yb * 12, q);
-            pair_body(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+            if constexpr (BODY == 3) pair_body(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+            else pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
         }
     } else if constexpr (!PF && BODY == 1) {
 #pragma unroll 1
@@ -629,7 +685,9 @@ BRI_D void dslash_body(int mode, const LL &ll, const typename LL::T *__restrict_
             const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 16u;
             f32_hops_cpasync(ll, in, site, nb, rsign, g, lbase, acc);
         } else {
-            f32_hops<VAR == 1 || VAR == 5, VAR == 4 ? 1 : VAR == 5 ? 2 : 0>(ll, in, site, nb, rsign, g, acc);
+            // VAR 5 (and 6, through k_dslash_r128): pair_body_s; VAR 7: pair_body
+            f32_hops<VAR == 1 || VAR >= 5, VAR == 4 ? 1 : VAR == 5 ? 2 : VAR == 7 ? 3 : 0>(ll, in, site, nb, rsign, g,
+                                                                                          acc);
         }
     } else {
         all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, g, acc);
@@ -662,7 +720,7 @@ __global__ void k_dslash(int mode, LL ll, const typename LL::T *__restrict__ in,
                          Geom g, double diag, const int *__restrict__ skip) {
     dslash_body<LL, VAR, CLOV>(mode, ll, in, out, g, diag, skip);
 }
-// launch variant 6: the variant-5 loop held to 128 registers (16 warps per SM)
+// launch variant 6: variant 5 held to 128 registers (16 warps per SM)
 template <class LL>
 __global__ void __maxnreg__(128) k_dslash_r128(int mode, LL ll, const typename LL::T *__restrict__ in,
                                                typename LL::T *__restrict__ out, Geom g, double diag,
@@ -844,7 +902,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     const int variant = threads >> 11;
     threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads[7] = {0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
+    static int max_threads[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
         const int v = (variant == 1 || variant == 2 || variant >= 4) ? variant : 0;
@@ -855,6 +913,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
                           : v == 4 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 4>)
                           : v == 5 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 5>)
                           : v == 6 ? cudaFuncGetAttributes(&attr, k_dslash_r128<LL>)
+                          : v == 7 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 7>)
                                    : cudaFuncGetAttributes(&attr, k_dslash<LL, 0>);
             max_threads[v] = e == cudaSuccess ? attr.maxThreadsPerBlock : 128;
             if (v == 2) {
@@ -870,6 +929,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         else if (v == 4) k_dslash<LL, 4><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 5) k_dslash<LL, 5><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 6) k_dslash_r128<LL><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else if (v == 7) k_dslash<LL, 7><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 2)
             k_dslash<LL, 2><<<grid, threads, threads * 4 * LL::SLOTS * 16, s>>>(mode, ll, (const T *)in, (T *)out, g,
                                                                                  diag, skip);

@@ -110,7 +110,7 @@ def test_kernel_variants_agree(gpu, prec, comp):
     x = torch.as_tensor(psi, device=gpu)
     outs = []
     for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256, 8192 + 128, 8192 + 256,
-                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128):
+                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128, 7 * 2048 + 128):
         op.set_threads(prec, 2, shape)
         outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
     for shape, o in outs[1:]:
@@ -142,8 +142,8 @@ def test_pair_kernel_matches_oracle(gpu, prec, comp, tol, L, bc):
 @pytest.mark.parametrize("prec,comp,tol", [("f32", "full", 1e-6), ("f32", "8param", 1e-6), ("f16", "2row", 2e-3)])
 @pytest.mark.parametrize("L,bc", [((3, 5, 4, 6), AP), ((4, 4, 4, 4), PER)])
 def test_pair_combined_body_matches_oracle(gpu, prec, comp, tol, L, bc):
-    """The loop that combines the hops d and -d before the gamma terms (launch
-    variants 5 and 6) against the oracle for D, D^dagger and the overlap kernel, with
+    """The loops that combine the hops d and -d before the gamma terms (launch
+    variants 5-7) against the oracle for D, D^dagger and the overlap kernel, with
     the Brillouin and the Wilson weights."""
     U, psi, W = _setup(L, bc, 60 + sum(L))
     for name in ("brillouin", "wilson"):
@@ -158,7 +158,7 @@ def test_pair_combined_body_matches_oracle(gpu, prec, comp, tol, L, bc):
                     oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) for r in range(psi.shape[0])]
         finally:
             oracle.reset_weights()
-        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128):
+        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128, 7 * 2048 + 128):
             op.set_threads(prec, 2, shape)
             out = op.apply(x, m0=0.05, prec=prec).cpu().numpy()
             outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
