@@ -33,8 +33,10 @@ LINK_BYTES = {  # bytes per site of the 40 stored hopping fields
     "f64-full": 40 * 144, "f32-full": 40 * 72, "f32-2row": 40 * 48, "f32-8param": 40 * 32,
     "f16-full": 40 * 36, "f16-2row": 40 * 24, "f16-8param": 40 * 16,
 }
-FLOPS_PER_SITE = 37296  # per right-hand side: 80 hops x 4 spins x 3 rows x 3 complex MACs (8 flops)
-                        # + 24 (1 + n) real FMAs per hop for the spin structure + diagonal
+FLOPS_PER_SITE = 34032  # per right-hand side: 80 hops x 4 spins x 3 rows x 3 complex MACs (8 flops)
+                        # + per (d, -d) pair of class n: sum and difference of the two colour
+                        # products (2 x 24 real FMAs), lambda term (24), gamma terms (24 n),
+                        # + diagonal (24); FMA = 2 flops
 
 
 def spinor_bytes(mode):
