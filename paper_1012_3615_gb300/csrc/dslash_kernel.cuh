@@ -5,16 +5,18 @@
 //
 // One thread per (site, right-hand side).  The 80 hops are walked as 40 pairs
 // (d, -d) over the stored canonical fields: W_d(x) for the forward hop and
-// W_d(x - d)^dagger for the reversed one.  All offsets, weights and gamma
-// permutations are compile-time constants (the hop loop is a template fold),
-// so each hop is: load W (coalesced 128-bit SoA chunks), load the neighbour
-// spinor, four colour mat-vecs, and the spin combination as real-coefficient
-// accumulations (gamma entries are +-1, +-i).
+// W_d(x - d)^dagger for the reversed one.  Each hop is: load W (coalesced
+// 128-bit SoA chunks), load the neighbour spinor, four colour mat-vecs; the spin
+// structure is taken as real-coefficient accumulations (gamma entries are +-1,
+// +-i), in most variants once per pair on the difference of the two colour
+// products.  FP64: the pair loop is a compile-time fold (offsets and gamma signs
+// constant); FP32 arithmetic: a loop over the hop table in the kernel
+// parameters (the unrolled form does not fit the instruction cache).
 //   mode 0: D;  mode 1: D^dagger = gamma_5 D gamma_5 (rho -> -rho, Sec. 1);
 //   mode 2: gamma_5 (D - rho): diagonal -rho + lambda_0, gamma_5 applied to the
 //           result (overlap kernel, Sec. 7.4).
 // Each link format is instantiated in its own translation unit (dslash_*.cu)
-// so the fully unrolled kernels compile in parallel.
+// so the kernels compile in parallel.
 #pragma once
 #include <utility>
 
@@ -78,56 +80,10 @@ template <> struct AccOf<double2> { using A = AccD; };
 
 BRI_D float2 f2(float v) { return make_float2(v, v); }
 
-// FP32 hop with packed FMAs: chi = W psi as sum_c' (psi.re * w + psi.im * (i w));
-// p is the neighbour spinor, already loaded
-template <int K, int SGN>
-BRI_D void hop_apply_p(const M3<float2> &W, const float2 p[12], float ph, float rsign, const Geom &g, AccF &acc) {
-    constexpr int n = off_class(K);
-    const float l = g.lam[n] * ph;
-    const float r = g.rho[n] * (ph * rsign);
-    float2 A[9], B[9];  // matrix entries w and i w (w = W or W^dagger entry)
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int cp = 0; cp < 3; cp++) {
-            const float2 w = SGN > 0 ? W.e[3 * c + cp] : make_float2(W.e[3 * cp + c].x, -W.e[3 * cp + c].y);
-            A[3 * c + cp] = w;
-            B[3 * c + cp] = make_float2(-w.y, w.x);
-        }
-#pragma unroll
-    for (int sp = 0; sp < 4; sp++) {
-        float2 chi[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            float2 t = __fmul2_rn(A[3 * c], f2(p[3 * sp].x));
-            t = __ffma2_rn(B[3 * c], f2(p[3 * sp].y), t);
-            t = __ffma2_rn(A[3 * c + 1], f2(p[3 * sp + 1].x), t);
-            t = __ffma2_rn(B[3 * c + 1], f2(p[3 * sp + 1].y), t);
-            t = __ffma2_rn(A[3 * c + 2], f2(p[3 * sp + 2].x), t);
-            t = __ffma2_rn(B[3 * c + 2], f2(p[3 * sp + 2].y), t);
-            chi[c] = t;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c++) acc.a[3 * sp + c] = __ffma2_rn(f2(l), chi[c], acc.a[3 * sp + c]);
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            const int dm = SGN * off_comp(K, mu);
-            if (dm == 0) continue;
-            const int s = gcol(mu, sp);
-            const int gr = gre(mu, s), gi = gim(mu, s);
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                if (gr != 0) acc.a[3 * s + c] = __ffma2_rn(f2(r * (float)(dm * gr)), chi[c], acc.a[3 * s + c]);
-                else acc.ai[3 * s + c] = __ffma2_rn(f2(r * (float)(dm * gi)), chi[c], acc.ai[3 * s + c]);
-            }
-        }
-    }
-}
-
-// Same arithmetic as hop_apply_p with the offset d a runtime value: the FP32
-// kernels loop over the 40 (d, -d) pairs instead of unrolling them, which keeps
-// the kernel small enough for the instruction cache (the unrolled form stalls
-// on instruction fetch).  The gamma terms are taken under warp-uniform branches
+// FP32 hop with packed FMAs, chi = W psi as sum_c' (psi.re * w + psi.im * (i w)),
+// with the offset d a runtime value: the FP32 kernels loop over the 40 (d, -d)
+// pairs instead of unrolling them, which keeps the kernel small enough for the
+// instruction cache (the unrolled form stalls on instruction fetch).  The gamma terms are taken under warp-uniform branches
 // on d_mu, so no arithmetic is wasted; the spin permutations stay compile-time.
 template <int SGN>
 BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, const int dm[4], AccF &acc) {
@@ -519,79 +475,91 @@ BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int sit
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int K, int SGN>
-BRI_D void hop_apply(const M3<float2> &W, const float2 *__restrict__ psi, float ph, float rsign, const Geom &g,
-                     AccF &acc) {
-    float2 p[12];
-    load_spinor(psi, p);
-    hop_apply_p<K, SGN>(W, p, ph, rsign, g, acc);
+// FP64 row products chi[c] = sum_c' w_cc' p_c' of spin sp as explicit FMA
+// chains (one multiply and five FMAs per real component): w = W (SGN = 1) or
+// W^dagger (SGN = -1).  Complex products followed by complex adds would cost
+// 16 FP64 operations per row instead of 12, and GB300's FP64 pipe is the limit.
+template <int SGN>
+BRI_D void mv64(const M3<double2> &W, const double2 p[12], int sp, double2 chi[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double re = 0, im = 0;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double2 e = SGN > 0 ? W.e[3 * c + k] : W.e[3 * k + c];
+            const double wx = e.x, wy = SGN > 0 ? e.y : -e.y;
+            const double2 v = p[3 * sp + k];
+            if (k == 0) {
+                re = wx * v.x;
+                im = wx * v.y;
+            } else {
+                re = fma(wx, v.x, re);
+                im = fma(wx, v.y, im);
+            }
+            re = fma(-wy, v.y, re);
+            im = fma(wy, v.x, im);
+        }
+        chi[c] = make_double2(re, im);
+    }
 }
 
-// one hop: offset of hypercube index K, reversed when SGN = -1 (then W is the
-// dagger of the stored field)
-template <int K, int SGN>
-BRI_D void hop_apply(const M3<double2> &W, const double2 *__restrict__ psi, float ph, float rsign, const Geom &g,
-                     AccD &accd) {
-    using T = double2;
-    using R = double;
-    T *acc = accd.a;
+// FP64 (d, -d) pair with offsets, weights and gamma signs fixed at compile time:
+// with q = phf phb the two hops add up to
+//   phf [ lam (chi_f + q chi_b) + rsign rho sum_mu d_mu gamma_mu (chi_f - q chi_b) ]
+// (the gamma terms once per pair, on the difference; cf is overwritten with it).
+template <int J, class LL>
+BRI_D void hop_pair(const LL &ll, const typename LL::T *__restrict__ in, int site, const SiteNb &nb,
+                    float rsign, const Geom &g, typename AccOf<typename LL::T>::A &acc) {
+    constexpr int K = canon_k(J);
     constexpr int n = off_class(K);
-    const R l = (R)g.lamd[n] * (R)ph;
-    const R r = (R)g.rhod[n] * (R)(ph * rsign);
-    T p[12];
-    load_spinor(psi, p);
+    if (g.lamd[n] == 0.0 && g.rhod[n] == 0.0) return;  // class not in the operator
+    float phf, phb;
+    const int yf = nb_index<K, 1>(nb, site, phf);
+    const int yb = nb_index<K, -1>(nb, site, phb);
+    double2 cf[12];
+    {
+        const M3<double2> W = ll.load(J, site);
+        double2 p[12];
+        load_spinor(in + (size_t)yf * 12, p);
 #pragma unroll
-    for (int sp = 0; sp < 4; sp++) {
-        T chi[3];
+        for (int sp = 0; sp < 4; sp++) mv64<1>(W, p, sp, cf + 3 * sp);
+    }
+    const double q = (double)(phf * phb);
+    const double L = g.lamd[n] * (double)phf, R = g.rhod[n] * (double)(phf * rsign);
+    {
+        const M3<double2> W = ll.load(J, yb);
+        double2 p[12];
+        load_spinor(in + (size_t)yb * 12, p);
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            T s;
-            if (SGN > 0) {
-                s = cmul(W.e[3 * c], p[3 * sp]);
-                s = cadd(s, cmul(W.e[3 * c + 1], p[3 * sp + 1]));
-                s = cadd(s, cmul(W.e[3 * c + 2], p[3 * sp + 2]));
-            } else {
-                s = cmulc(W.e[c], p[3 * sp]);
-                s = cadd(s, cmulc(W.e[3 + c], p[3 * sp + 1]));
-                s = cadd(s, cmulc(W.e[6 + c], p[3 * sp + 2]));
+        for (int sp = 0; sp < 4; sp++) {
+            double2 cb[3];
+            mv64<-1>(W, p, sp, cb);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                double2 &f = cf[3 * sp + c];
+                const double sx = fma(q, cb[c].x, f.x), sy = fma(q, cb[c].y, f.y);
+                f.x = fma(-q, cb[c].x, f.x);
+                f.y = fma(-q, cb[c].y, f.y);
+                acc.a[3 * sp + c].x = fma(L, sx, acc.a[3 * sp + c].x);
+                acc.a[3 * sp + c].y = fma(L, sy, acc.a[3 * sp + c].y);
             }
-            chi[c] = s;
         }
+    }
 #pragma unroll
-        for (int c = 0; c < 3; c++) acc_re(acc[3 * sp + c], l, chi[c]);
+    for (int mu = 0; mu < 4; mu++) {
+        const int dm = off_comp(K, mu);
+        if (dm == 0) continue;
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            const int dm = SGN * off_comp(K, mu);
-            if (dm == 0) continue;
+        for (int sp = 0; sp < 4; sp++) {
             // row s of gamma_mu has its entry in column sp
             const int s = gcol(mu, sp);
             const int gr = gre(mu, s), gi = gim(mu, s);
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                if (gr != 0) acc_re(acc[3 * s + c], r * (R)(dm * gr), chi[c]);
-                else acc_im(acc[3 * s + c], r * (R)(dm * gi), chi[c]);
+                if (gr != 0) acc_re(acc.a[3 * s + c], R * (double)(dm * gr), cf[3 * sp + c]);
+                else acc_im(acc.a[3 * s + c], R * (double)(dm * gi), cf[3 * sp + c]);
             }
         }
-    }
-}
-
-template <int J, class LL>
-BRI_D void hop_pair(const LL &ll, const typename LL::T *__restrict__ in, int site, const SiteNb &nb,
-                    float rsign, const Geom &g, typename AccOf<typename LL::T>::A &acc) {
-    using T = typename LL::T;
-    constexpr int K = canon_k(J);
-    if (g.lamd[off_class(K)] == 0.0 && g.rhod[off_class(K)] == 0.0) return;  // class not in the operator
-    {
-        float ph;
-        const int y = nb_index<K, 1>(nb, site, ph);
-        M3<T> W = ll.load(J, site);
-        hop_apply<K, 1>(W, in + (size_t)y * 12, ph, rsign, g, acc);
-    }
-    {
-        float ph;
-        const int y = nb_index<K, -1>(nb, site, ph);
-        M3<T> W = ll.load(J, y);
-        hop_apply<K, -1>(W, in + (size_t)y * 12, ph, rsign, g, acc);
     }
 }
 
