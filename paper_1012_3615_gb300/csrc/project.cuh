@@ -33,30 +33,41 @@ BRI_D void herm_eig3(double2 H[9], double2 V[9], double e[3]) {
         for (int pq = 0; pq < 3; pq++) {
             const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
             double2 h = H[3 * p + q];
-            double gabs = sqrt(cnorm2(h));
-            if (gabs == 0.0) continue;
+            const double n2 = cnorm2(h);
+            if (n2 == 0.0) continue;
+            // FP64 divisions and square roots are long sequences on the FP64
+            // pipe: one reciprocal square root serves |h|^-1, one the cosine
+            const double ig = rsqrt(n2);
             double a = H[4 * p].x, b = H[4 * q].x;
-            double tau = (b - a) / (2.0 * gabs);
-            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-            double2 ep = make_double2(h.x / gabs, -h.y / gabs);  // e^{-i arg h}
+            double tau = 0.5 * (b - a) * ig;
+            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+            double c = rsqrt(fma(t, t, 1.0)), s = t * c;
+            double2 ep = make_double2(h.x * ig, -h.y * ig);  // e^{-i arg h}
             double2 se = cscale(ep, s), ce = cscale(ep, c);
-            // H <- H J, V <- V J   (columns p, q)
+            // H <- H J, V <- V J   (columns p, q), as FMA chains:
+            //   new p = c x_p - x_q se,  new q = s x_p + x_q ce
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 double2 hp = H[3 * i + p], hq = H[3 * i + q];
-                H[3 * i + p] = csub(cscale(hp, c), cmul(hq, se));
-                H[3 * i + q] = cadd(cscale(hp, s), cmul(hq, ce));
+                H[3 * i + p] = make_double2(fma(-hq.x, se.x, fma(hq.y, se.y, c * hp.x)),
+                                            fma(-hq.x, se.y, fma(-hq.y, se.x, c * hp.y)));
+                H[3 * i + q] = make_double2(fma(hq.x, ce.x, fma(-hq.y, ce.y, s * hp.x)),
+                                            fma(hq.x, ce.y, fma(hq.y, ce.x, s * hp.y)));
                 double2 vp = V[3 * i + p], vq = V[3 * i + q];
-                V[3 * i + p] = csub(cscale(vp, c), cmul(vq, se));
-                V[3 * i + q] = cadd(cscale(vp, s), cmul(vq, ce));
+                V[3 * i + p] = make_double2(fma(-vq.x, se.x, fma(vq.y, se.y, c * vp.x)),
+                                            fma(-vq.x, se.y, fma(-vq.y, se.x, c * vp.y)));
+                V[3 * i + q] = make_double2(fma(vq.x, ce.x, fma(-vq.y, ce.y, s * vp.x)),
+                                            fma(vq.x, ce.y, fma(vq.y, ce.x, s * vp.y)));
             }
-            // H <- J^dagger H   (rows p, q)
+            // H <- J^dagger H   (rows p, q):
+            //   new p = c y_p - conj(se) y_q,  new q = s y_p + conj(ce) y_q
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 double2 hp = H[3 * p + j], hq = H[3 * q + j];
-                H[3 * p + j] = csub(cscale(hp, c), cmul(cconj(se), hq));
-                H[3 * q + j] = cadd(cscale(hp, s), cmul(cconj(ce), hq));
+                H[3 * p + j] = make_double2(fma(-se.x, hq.x, fma(-se.y, hq.y, c * hp.x)),
+                                            fma(-se.x, hq.y, fma(se.y, hq.x, c * hp.y)));
+                H[3 * q + j] = make_double2(fma(ce.x, hq.x, fma(ce.y, hq.y, s * hp.x)),
+                                            fma(ce.x, hq.y, fma(-ce.y, hq.x, s * hp.y)));
             }
             H[3 * p + q] = make_double2(0, 0);
             H[3 * q + p] = make_double2(0, 0);
@@ -69,15 +80,15 @@ BRI_D void herm_eig3(double2 H[9], double2 V[9], double e[3]) {
     e[2] = H[8].x;
 }
 
-// sum_i asin(kappa/s_i) - t and its derivative
-BRI_D double branch_a(const double s[3], double kappa, double t, double &deriv) {
+// sum_i asin(kappa/s_i) - t and its derivative (is: the reciprocals 1/s_i)
+BRI_D double branch_a(const double s[3], const double is[3], double kappa, double t, double &deriv) {
     double f = -t, d = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        double r = kappa / s[i];
+        double r = kappa * is[i];
         r = fmin(1.0, fmax(-1.0, r));
         f += asin(r);
-        d += 1.0 / sqrt(fmax(s[i] * s[i] - kappa * kappa, 1e-300));
+        d += rsqrt(fmax(fma(s[i], s[i], -kappa * kappa), 1e-300));
     }
     deriv = d;
     return f;
@@ -86,11 +97,12 @@ BRI_D double branch_a(const double s[3], double kappa, double t, double &deriv) 
 // root of branch A for target t, |t| <= M guaranteed by the caller
 BRI_D double solve_branch_a(const double s[3], double t) {
     double lo = -s[2], hi = s[2];
-    double kappa = t / (1.0 / s[0] + 1.0 / s[1] + 1.0 / s[2]);
+    const double is[3] = {1.0 / s[0], 1.0 / s[1], 1.0 / s[2]};
+    double kappa = t / (is[0] + is[1] + is[2]);
     kappa = fmin(hi, fmax(lo, kappa));
     for (int it = 0; it < 200; it++) {
         double d;
-        double f = branch_a(s, kappa, t, d);
+        double f = branch_a(s, is, kappa, t, d);
         if (f == 0.0) break;
         if (f > 0) hi = kappa; else lo = kappa;
         double kn = kappa - f / d;

@@ -6,7 +6,9 @@ at a time (it builds the 80 hops of a sampled site from the links on the spot):
     links exp(i0.4H), Z2 source): the true residual b - D x at sampled sites;
   * 24^3x48 batched solve of the 12 spin-colour point sources (FP16 hops,
     m0 = 0): the residual at the source site, its neighbours and random sites;
-  * 32^3x64 applies for every storage format and 4 right-hand sides;
+  * 32^3x64 applies for every storage format and 4 right-hand sides, and the
+    benchmark's own workload (FP32 full hops, 1 RHS, default launch shape) and
+    its FP64 apply;
   * 12^4 fermion force: central finite differences of Re chi^dagger D psi in
     single link entries, evaluated over the 54 sites whose hops contain that
     link."""
@@ -116,6 +118,34 @@ def test_storage_formats_and_rhs_32x32x32x64(gpu):
             got = out[r][sites]
             assert np.linalg.norm(got - refs[r]) <= tol * np.linalg.norm(refs[r]), (prec, comp, r)
     del op, U, psi
+    torch.cuda.empty_cache()
+
+
+def test_benchmark_workload_32x32x32x64(gpu):
+    """The benchmark's own workload and launch: links exp(i0.3H) (seed 1015),
+    Gaussian FP32 spinor (seed 1115), FP32 full hops at the default launch
+    shape, ten applies into the same output as the timed loop does; then the
+    FP64 apply of the same field.  Sampled sites against the oracle."""
+    L = (32, 32, 32, 64)
+    V = synth.volume(L)
+    U = synth.random_su3_links_torch(L, 0.3, 1015, device=gpu)
+    x = synth.gaussian_spinor_torch(L, 1, 1115, device=gpu, dtype=torch.complex64)
+    op = Brillouin(L, AP)
+    op.build_hops(U, prec="f32", comp="full")
+    out = torch.empty_like(x)
+    for _ in range(10):
+        op.apply(x, 0.0, prec="f32", out=out)
+    sites = np.concatenate([[0, 31, 32 * 32 - 1, V // 2, V - 1], np.random.default_rng(11).integers(0, V, 7)])
+    Uh = U.cpu().numpy()
+    psi = x[0].cpu().numpy().astype(np.complex128)
+    ref = oracle.apply_sites(L, AP, Uh, 0.0, psi, sites)
+    got = out[0].cpu().numpy()[sites]
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+    del out
+    x64 = x.to(torch.complex128)  # the FP64 fields stay next to the FP32 ones
+    got64 = op.apply(x64, 0.0).cpu().numpy()[0][sites]
+    assert np.abs(got64 - ref).max() <= 1e-13 * np.abs(ref).max()
+    del op, U, x, x64
     torch.cuda.empty_cache()
 
 
