@@ -39,7 +39,7 @@ void bri_host_apply_free(bri_ctx *ctx) {
     ctx->hw = nullptr;
 }
 
-static constexpr int MAX_SLABS = 16;
+static constexpr int MAX_SLABS = 32;
 
 static bri_status ensure_host_work(bri_ctx *ctx, size_t bytes) {
     HostApplyWork *w = ctx->hw;
