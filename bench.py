@@ -529,6 +529,19 @@ def solve_bench(args, dev):
         res["fp64_first_source"] = dict(inf1[0], seconds=time.perf_counter() - t0)
         res["speedup_batched_vs_sequential_mixed"] = res["sequential_12_mixed_f16"]["seconds"] / res["batched_12"]["seconds"]
         res["speedup_batched_vs_12x_fp64"] = 12 * res["fp64_first_source"]["seconds"] / res["batched_12"]["seconds"]
+        # the same batched solve with FP32 2-row fields as the inner precision (mode 4):
+        # the apply is ALU-bound, so FP32 fields cost about what FP16 ones do, and the
+        # FP32 inner solves need fewer defect-correction cycles (FP64 residual applies)
+        op.store_hops("f32", "2row")
+        op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=4)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x4, info4 = op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=4)
+        torch.cuda.synchronize()
+        res["batched_12_f32_fields"] = {"seconds": time.perf_counter() - t0, "iters": [i["iters"] for i in info4],
+                                        "outer": [i["outer_iters"] for i in info4],
+                                        "true_resid_max": max(i["true_resid"] for i in info4),
+                                        "status": sorted(set(i["status"] for i in info4))}
         out["solve_24x24x24x48_12_point_sources"] = res
     return out
 

@@ -152,13 +152,17 @@ typedef struct {
  *   mode 1: FP64 defect correction around an FP32 BiCGstab (FP32 hops as
  *           last stored, FP32 spinors, FP64 dot products).
  *   mode 2: as mode 1 with the FP16 hopping fields.
+ *   Modes 1 and 2 solve the right-hand sides one after the other.
  *   mode 3: batched: all nrhs right-hand sides advance together through one
  *           multi-RHS apply per step (mode-2 inner precision), each with its
  *           own BiCGstab scalars, inside one CUDA graph per block of steps.
+ *   mode 4: as mode 3 with the FP32 hopping fields (mode-1 inner precision).
  * x: device, [nrhs][V][4][3] complex128, used as the initial guess and
  * overwritten with the solution; b: device, same layout.  info: host array of
  * nrhs entries (may be null).  Synchronises the stream.  Returns BRI_OK when
- * every right-hand side converged, otherwise the first failing status. */
+ * every right-hand side converged, otherwise the first failing status (a
+ * right-hand side that fails to converge does not stop the others; BRI_EINVAL
+ * for a mode outside 0..4). */
 bri_status bri_solve(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol,
                      int maxit, int mode, bri_solve_info *info, void *stream);
 

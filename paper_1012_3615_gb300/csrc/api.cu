@@ -194,7 +194,7 @@ bri_status bri_solve(bri_ctx *ctx, double *x, const double *b, int nrhs, double 
         return bri_fail(ctx, BRI_EINVAL, "x and b must be 16-byte aligned device pointers");
     if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
     if (!(tol > 0) || maxit < 1) return bri_fail(ctx, BRI_EINVAL, "tol must be > 0 and maxit >= 1");
-    if (mode < 0 || mode > 3) return bri_fail(ctx, BRI_EINVAL, "mode must be 0..3");
+    if (mode < 0 || mode > 4) return bri_fail(ctx, BRI_EINVAL, "mode must be 0..4");
     if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
     const size_t bytes = 16 * 12 * (size_t)ctx->g.V * nrhs;
     if ((const char *)x < (const char *)b + bytes && (const char *)b < (const char *)x + bytes)

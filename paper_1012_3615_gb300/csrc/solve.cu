@@ -648,19 +648,23 @@ bri_status bri_solve_impl(bri_ctx *ctx, double *x, const double *b, int nrhs, do
         BRI_RETURN_IF(ensure_work(ctx, 1, true, false));
         if (!ctx->work->r64) BRI_TRY_CUDA(ctx, cudaMalloc(&ctx->work->r64, sizeof(double2) * n * ctx->work->nrhs));
     } else {
-        if (mode != 3 && nrhs > 1) {
-            // sequential right-hand sides in modes 1, 2
+        if (mode <= 2 && nrhs > 1) {
+            // sequential right-hand sides in modes 1, 2; a right-hand side that
+            // does not converge does not stop the others (its status is returned)
+            bri_status worst = BRI_OK;
             for (int r = 0; r < nrhs; r++) {
-                BRI_RETURN_IF(bri_solve_impl(ctx, x + 2 * r * n, b + 2 * r * n, 1, m0, tol, maxit, mode,
-                                             info ? info + r : nullptr, user));
+                const bri_status st = bri_solve_impl(ctx, x + 2 * r * n, b + 2 * r * n, 1, m0, tol, maxit, mode,
+                                                     info ? info + r : nullptr, user);
+                if (st != BRI_OK && st != BRI_ENOTCONV && st != BRI_EBREAKDOWN && st != BRI_ENAN) return st;
+                if (st != BRI_OK && worst == BRI_OK) worst = st;
             }
-            return BRI_OK;
+            return worst;
         }
         BRI_RETURN_IF(ensure_work(ctx, nrhs, false, true));
     }
     cudaStream_t s = user ? user : ctx->work->own;
     if (!user) BRI_TRY_CUDA(ctx, cudaDeviceSynchronize());
-    const bri_prec prec = mode == 1 ? BRI_F32 : BRI_F16;
+    const bri_prec prec = mode == 1 || mode == 4 ? BRI_F32 : BRI_F16;
     if (mode != 0) {
         const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
         if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "inner-precision hopping fields not built");

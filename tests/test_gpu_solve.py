@@ -1,6 +1,7 @@
 """GPU BiCGstab (Sec. 6.4): FP64, mixed-precision defect correction and the
-batched multi-RHS solve, all to a true FP64 residual of 1e-10, plus the
-failure statuses (non-convergence, NaN, zero source)."""
+batched multi-RHS solve (FP16 and FP32 inner fields), all to a true FP64
+residual of 1e-10, plus the failure statuses (non-convergence, NaN, zero
+source) and their handling across right-hand sides."""
 import numpy as np
 import pytest
 import torch
@@ -60,6 +61,37 @@ def test_batched_point_sources(gpu):
         assert _true_resid(L, AP, W, 0.0, xs[r], b[r]) <= 1e-10
     x0s, info0 = op.solve(torch.as_tensor(b[:2], device=gpu), m0=0.0, tol=1e-12, mode=0)
     assert np.linalg.norm(xs[:2] - x0s.cpu().numpy()) / np.linalg.norm(x0s.cpu().numpy()) < 1e-8
+
+
+def test_batched_point_sources_fp32_fields(gpu):
+    """Mode 4: the batched solve with the FP32 hopping fields as inner precision."""
+    L = (4, 4, 4, 4)
+    U = synth.random_su3_links(L, 0.35, 5)
+    b, x0 = synth.point_sources(L, 6)
+    W = oracle.build_hops(L, U)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp="2row")
+    x, info = op.solve(torch.as_tensor(b, device=gpu), m0=0.0, tol=1e-10, mode=4)
+    assert all(i["status"] == "BRI_OK" for i in info), info
+    xs = x.cpu().numpy()
+    for r in range(12):
+        assert _true_resid(L, AP, W, 0.0, xs[r], b[r]) <= 1e-10
+    # FP32 inner solves need fewer defect-correction cycles than FP16 ones
+    assert max(i["outer_iters"] for i in info) <= 3
+
+
+def test_sequential_modes_continue_after_a_failed_rhs(gpu):
+    """Modes 1 and 2 take the right-hand sides one after the other; a NaN in the
+    first does not stop the second, and the call returns the failing status."""
+    L = (3, 3, 3, 4)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(synth.random_su3_links(L, 0.3, 9), device=gpu), prec="f32", comp="2row")
+    b = torch.as_tensor(synth.gaussian_spinor(L, 2, 10), device=gpu)
+    b[0, 3, 0, 1] = float("nan")
+    x, info = op.solve(b, m0=0.1, tol=1e-10, mode=1)
+    assert info[0]["status"] == "BRI_ENAN" and info[1]["status"] == "BRI_OK", info
+    assert info[1]["true_resid"] <= 1e-10
+    assert torch.isfinite(x[1]).all()
 
 
 def test_singular_operator_reports_nonconvergence(gpu):
