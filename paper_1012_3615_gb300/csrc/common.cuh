@@ -83,18 +83,39 @@ template <typename T> BRI_HD double cnorm2(T a) { return (double)a.x * a.x + (do
 template <typename T> struct M3 {
     T e[9];
 };
-template <typename T> BRI_HD M3<T> m3_mul(const M3<T> &a, const M3<T> &b) {
+// c = acc + a b (ACC) or a b, each entry one multiply and five (or six) FMAs
+// per real component: complex products followed by complex adds cost a third
+// more on the FP64 pipe
+template <bool ACC, typename T>
+BRI_HD M3<T> m3_mul_acc(const M3<T> &acc, const M3<T> &a, const M3<T> &b) {
     M3<T> c;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            T s = cmul(a.e[3 * i], b.e[j]);
-            s = cadd(s, cmul(a.e[3 * i + 1], b.e[3 + j]));
-            s = cadd(s, cmul(a.e[3 * i + 2], b.e[6 + j]));
-            c.e[3 * i + j] = s;
+            const T a0 = a.e[3 * i], a1 = a.e[3 * i + 1], a2 = a.e[3 * i + 2];
+            const T b0 = b.e[j], b1 = b.e[3 + j], b2 = b.e[6 + j];
+            auto re = ACC ? fma(a0.x, b0.x, acc.e[3 * i + j].x) : a0.x * b0.x;
+            auto im = ACC ? fma(a0.x, b0.y, acc.e[3 * i + j].y) : a0.x * b0.y;
+            re = fma(-a0.y, b0.y, re);
+            im = fma(a0.y, b0.x, im);
+            re = fma(a1.x, b1.x, re);
+            im = fma(a1.x, b1.y, im);
+            re = fma(-a1.y, b1.y, re);
+            im = fma(a1.y, b1.x, im);
+            re = fma(a2.x, b2.x, re);
+            im = fma(a2.x, b2.y, im);
+            re = fma(-a2.y, b2.y, re);
+            im = fma(a2.y, b2.x, im);
+            c.e[3 * i + j].x = re;
+            c.e[3 * i + j].y = im;
         }
     return c;
+}
+template <typename T> BRI_HD M3<T> m3_mul(const M3<T> &a, const M3<T> &b) { return m3_mul_acc<false>(a, a, b); }
+// acc + a b
+template <typename T> BRI_HD M3<T> m3_mad(const M3<T> &acc, const M3<T> &a, const M3<T> &b) {
+    return m3_mul_acc<true>(acc, a, b);
 }
 template <typename T> BRI_HD M3<T> m3_dag(const M3<T> &a) {
     M3<T> c;

@@ -48,7 +48,7 @@ __global__ void k_dp_level(int n, const int *__restrict__ klist, int nk, const d
         } else {
             const int y = site + (c > 0 ? nb.fw[mu] : nb.bw[mu]);
             const int kk = k - c * p3;
-            acc = m3_add(acc, m3_mul(F, A[(size_t)kk * g.V + y]));
+            acc = m3_mad(acc, F, A[(size_t)kk * g.V + y]);
         }
     }
     const double inv = 1.0 / n;

@@ -64,7 +64,7 @@ __global__ void k_na_level(int n, ClassList cl, const double2 *__restrict__ U, M
             acc = F;
         } else {
             const int y = site + (c > 0 ? nb.fw[mu] : nb.bw[mu]);
-            acc = m3_add(acc, m3_mul(F, A[(size_t)(k - c * p3) * g.V + y]));
+            acc = m3_mad(acc, F, A[(size_t)(k - c * p3) * g.V + y]);
         }
     }
     for (int i = 0; i < 9; i++) acc.e[i] = cscale(acc.e[i], 1.0 / n);

@@ -76,7 +76,7 @@ __global__ void k_ape(const double2 *__restrict__ U, double2 *__restrict__ Vout,
             const M3<double2> a = link_dir(U, g, x, nu, sg);
             const M3<double2> b = link_dir(U, g, xn, mu, 1);
             const M3<double2> c = m3_dag(link_dir(U, g, xm, nu, sg));
-            S = m3_add(S, m3_mul(m3_mul(a, b), c));
+            S = m3_mad(S, m3_mul(a, b), c);
         }
     }
     const M3<double2> u = link_dir(U, g, x, mu, 1);
