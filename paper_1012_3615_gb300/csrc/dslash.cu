@@ -100,25 +100,26 @@ static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void
             return BRI_OK;
         }
         if ((threads >> 11) == 3) threads = 128;  // no pair copy for this storage: plain kernel
+        const int VP = (g.V + 31) & ~31;          // sites per field of the blocked FP32/FP16 layout
         if (prec == BRI_F32) {
             if (st.comp == BRI_LINK_FULL)
-                dslash_launch(mode, LinkF32<BRI_LINK_FULL>{(const float4 *)st.a, (const float2 *)st.b, g.V}, in, out, nrhs,
+                dslash_launch(mode, LinkF32<BRI_LINK_FULL>{(const float4 *)st.a, (const float2 *)st.b, VP}, in, out, nrhs,
                        g, diag, skip, threads, s);
             else if (st.comp == BRI_LINK_2ROW)
-                dslash_launch(mode, LinkF32<BRI_LINK_2ROW>{(const float4 *)st.a, nullptr, g.V}, in, out, nrhs, g, diag, skip,
+                dslash_launch(mode, LinkF32<BRI_LINK_2ROW>{(const float4 *)st.a, nullptr, VP}, in, out, nrhs, g, diag, skip,
                        threads, s);
             else
-                dslash_launch(mode, LinkF32<BRI_LINK_8PARAM>{(const float4 *)st.a, nullptr, g.V}, in, out, nrhs, g, diag,
+                dslash_launch(mode, LinkF32<BRI_LINK_8PARAM>{(const float4 *)st.a, nullptr, VP}, in, out, nrhs, g, diag,
                        skip, threads, s);
         } else {
             if (st.comp == BRI_LINK_FULL)
-                dslash_launch(mode, LinkF16<BRI_LINK_FULL>{(const uint4 *)st.a, st.b, g.V}, in, out, nrhs, g, diag, skip,
+                dslash_launch(mode, LinkF16<BRI_LINK_FULL>{(const uint4 *)st.a, st.b, VP}, in, out, nrhs, g, diag, skip,
                        threads, s);
             else if (st.comp == BRI_LINK_2ROW)
-                dslash_launch(mode, LinkF16<BRI_LINK_2ROW>{(const uint4 *)st.a, st.b, g.V}, in, out, nrhs, g, diag, skip,
+                dslash_launch(mode, LinkF16<BRI_LINK_2ROW>{(const uint4 *)st.a, st.b, VP}, in, out, nrhs, g, diag, skip,
                        threads, s);
             else
-                dslash_launch(mode, LinkF16<BRI_LINK_8PARAM>{(const uint4 *)st.a, nullptr, g.V}, in, out, nrhs, g, diag,
+                dslash_launch(mode, LinkF16<BRI_LINK_8PARAM>{(const uint4 *)st.a, nullptr, VP}, in, out, nrhs, g, diag,
                        skip, threads, s);
         }
     }

@@ -77,6 +77,13 @@ __global__ void k_project_batch(const M3<double2> *__restrict__ A, M3<double2> *
 }
 
 // ---- reduced-precision stores -------------------------------------------------
+// chunk q (of nq) of field j at site s in the 32-site blocked layout of the
+// FP32/FP16 stores (links.cuh): [40][Vp/32][nq][32], Vp = V rounded up to 32
+BRI_D size_t blk_idx(int j, int q, int s, int nq, size_t VP) {
+    return ((size_t)j * VP + (s & ~31)) * nq + (size_t)q * 32 + (s & 31);
+}
+BRI_HD size_t pad32(size_t V) { return (V + 31) & ~(size_t)31; }
+
 template <bri_comp C> __global__ void k_store_f32(const double2 *__restrict__ h, LinkStore st, Geom g) {
     const int site = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
@@ -85,23 +92,23 @@ template <bri_comp C> __global__ void k_store_f32(const double2 *__restrict__ h,
 #pragma unroll
     for (int e = 0; e < 9; e++) w[e] = h[((size_t)j * 9 + e) * g.V + site];
     float4 *a = (float4 *)st.a;
-    const size_t V = g.V;
+    const size_t VP = pad32(g.V);
     if (C == BRI_LINK_FULL) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
-            a[((size_t)j * 4 + q) * V + site] =
+            a[blk_idx(j, q, site, 4, VP)] =
                 make_float4((float)w[2 * q].x, (float)w[2 * q].y, (float)w[2 * q + 1].x, (float)w[2 * q + 1].y);
-        ((float2 *)st.b)[(size_t)j * V + site] = make_float2((float)w[8].x, (float)w[8].y);
+        ((float2 *)st.b)[(size_t)j * VP + site] = make_float2((float)w[8].x, (float)w[8].y);
     } else if (C == BRI_LINK_2ROW) {
 #pragma unroll
         for (int q = 0; q < 3; q++)
-            a[((size_t)j * 3 + q) * V + site] =
+            a[blk_idx(j, q, site, 3, VP)] =
                 make_float4((float)w[2 * q].x, (float)w[2 * q].y, (float)w[2 * q + 1].x, (float)w[2 * q + 1].y);
     } else {
         float p[8];
         eight_params(w, p);
-        a[((size_t)j * 2 + 0) * V + site] = make_float4(p[0], p[1], p[2], p[3]);
-        a[((size_t)j * 2 + 1) * V + site] = make_float4(p[4], p[5], p[6], p[7]);
+        a[blk_idx(j, 0, site, 2, VP)] = make_float4(p[0], p[1], p[2], p[3]);
+        a[blk_idx(j, 1, site, 2, VP)] = make_float4(p[4], p[5], p[6], p[7]);
     }
 }
 
@@ -118,22 +125,22 @@ template <bri_comp C> __global__ void k_store_f16(const double2 *__restrict__ h,
 #pragma unroll
     for (int e = 0; e < 9; e++) w[e] = h[((size_t)j * 9 + e) * g.V + site];
     uint4 *a = (uint4 *)st.a;
-    const size_t V = g.V;
+    const size_t VP = pad32(g.V);
     if (C == BRI_LINK_FULL) {
 #pragma unroll
         for (int q = 0; q < 2; q++)
-            a[((size_t)j * 2 + q) * V + site] =
+            a[blk_idx(j, q, site, 2, VP)] =
                 make_uint4(pack_h2(w[4 * q].x, w[4 * q].y), pack_h2(w[4 * q + 1].x, w[4 * q + 1].y),
                            pack_h2(w[4 * q + 2].x, w[4 * q + 2].y), pack_h2(w[4 * q + 3].x, w[4 * q + 3].y));
-        ((uint32_t *)st.b)[(size_t)j * V + site] = pack_h2(w[8].x, w[8].y);
+        ((uint32_t *)st.b)[(size_t)j * VP + site] = pack_h2(w[8].x, w[8].y);
     } else if (C == BRI_LINK_2ROW) {
-        a[(size_t)j * V + site] = make_uint4(pack_h2(w[0].x, w[0].y), pack_h2(w[1].x, w[1].y),
-                                             pack_h2(w[2].x, w[2].y), pack_h2(w[3].x, w[3].y));
-        ((uint2 *)st.b)[(size_t)j * V + site] = make_uint2(pack_h2(w[4].x, w[4].y), pack_h2(w[5].x, w[5].y));
+        a[blk_idx(j, 0, site, 1, VP)] = make_uint4(pack_h2(w[0].x, w[0].y), pack_h2(w[1].x, w[1].y),
+                                                   pack_h2(w[2].x, w[2].y), pack_h2(w[3].x, w[3].y));
+        ((uint2 *)st.b)[(size_t)j * VP + site] = make_uint2(pack_h2(w[4].x, w[4].y), pack_h2(w[5].x, w[5].y));
     } else {
         float p[8];
         eight_params(w, p);
-        a[(size_t)j * V + site] =
+        a[blk_idx(j, 0, site, 1, VP)] =
             make_uint4(pack_h2(p[0], p[1]), pack_h2(p[2], p[3]), pack_h2(p[4], p[5]), pack_h2(p[6], p[7]));
     }
 }
@@ -242,9 +249,9 @@ bri_status bri_hops_store_impl(bri_ctx *ctx, bri_prec prec, bri_comp comp, cudaS
     }
     st.valid = false;
     if (!st.a) {
-        BRI_TRY_CUDA(ctx, cudaMalloc(&st.a, store_bytes_a(prec, comp) * NCANON * V));
+        BRI_TRY_CUDA(ctx, cudaMalloc(&st.a, store_bytes_a(prec, comp) * NCANON * pad32(V)));
         size_t nb = store_bytes_b(prec, comp);
-        if (nb) BRI_TRY_CUDA(ctx, cudaMalloc(&st.b, nb * NCANON * V));
+        if (nb) BRI_TRY_CUDA(ctx, cudaMalloc(&st.b, nb * NCANON * pad32(V)));
     }
     st.comp = comp;
     const int T = 128;

@@ -1,8 +1,12 @@
 // Storage formats of the 40 hopping fields and their device-side loaders.
 //
-// Every field j is stored structure-of-arrays over sites in 16-byte chunks
-// ([40][chunks][V]), so a warp reading one chunk of 32 consecutive sites issues
-// fully coalesced 128-bit loads:
+// FP64 fields are stored structure-of-arrays over sites ([40][9][V]).  The FP32
+// and FP16 fields are cut into 16-byte chunks stored in blocks of 32 sites,
+// [40][Vp/32][chunks][32] with Vp = V rounded up to 32: a warp reading one
+// chunk of 32 consecutive sites issues fully coalesced 128-bit loads, and the
+// chunks of one site lie at compile-time offsets (q x 512 bytes) from its first
+// one, so a field costs one address computation, not one per chunk.  The last
+// 8 or 4 bytes of a full or 2-row field go to a second array [40][Vp]:
 //   FP64 full    9 x double2                      144 B
 //   FP32 full    4 x float4 + 1 x float2           72 B
 //   FP32 2-row   3 x float4                        48 B
@@ -111,23 +115,28 @@ template <bri_comp C> struct LinkF32 {
     using T = float2;
     // 16-byte shared-memory slots one field occupies when prefetched
     static constexpr int SLOTS = C == BRI_LINK_FULL ? 5 : C == BRI_LINK_2ROW ? 3 : 2;
+    static constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;  // float4 chunks
     const float4 *__restrict__ a;
     const float2 *__restrict__ b;
-    int V;
+    int VP;  // sites per field, V rounded up to a multiple of 32
+    // first chunk of field j at site s (chunk q follows at + 32 q)
+    BRI_D const float4 *chunk0(int j, int s) const {
+        return a + ((size_t)j * VP + (s & ~31)) * NQ + (s & 31);
+    }
     // shared-memory slots are chunk-major across the block: chunk q of this
     // thread's field at dst + q * stride (stride = 16 bytes x threads), so a
     // warp's 16-byte accesses are consecutive and free of bank conflicts
     BRI_D void prefetch(int j, int site, uint32_t dst, uint32_t stride) const {
-        constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;
+        const float4 *p = chunk0(j, site);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) cp_async16(dst + stride * q, a + ((size_t)j * NQ + q) * V + site);
-        if (C == BRI_LINK_FULL) cp_async8(dst + stride * 4, b + (size_t)j * V + site);
+        for (int q = 0; q < NQ; q++) cp_async16(dst + stride * q, p + 32 * q);
+        if (C == BRI_LINK_FULL) cp_async8(dst + stride * 4, b + (size_t)j * VP + site);
     }
     BRI_D void prefetch_field_l2(int j, int site) const {
-        constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;
+        const float4 *p = chunk0(j, site);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) prefetch_l2(a + ((size_t)j * NQ + q) * V + site);
-        if (C == BRI_LINK_FULL) prefetch_l2(b + (size_t)j * V + site);
+        for (int q = 0; q < NQ; q++) prefetch_l2(p + 32 * q);
+        if (C == BRI_LINK_FULL) prefetch_l2(b + (size_t)j * VP + site);
     }
     BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
         M3<float2> m;
@@ -136,9 +145,8 @@ template <bri_comp C> struct LinkF32 {
             float p[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             return from_eight(p);
         }
-        constexpr int NQ = C == BRI_LINK_FULL ? 4 : 3;
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
+        for (int q = 0; q < (C == BRI_LINK_FULL ? 4 : 3); q++) {
             float4 v = lds4(src + stride * q);
             m.e[2 * q] = make_float2(v.x, v.y);
             m.e[2 * q + 1] = make_float2(v.z, v.w);
@@ -153,27 +161,20 @@ template <bri_comp C> struct LinkF32 {
     }
     BRI_D M3<float2> load(int j, int site) const {
         M3<float2> m;
-        if (C == BRI_LINK_FULL) {
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                float4 v = a[((size_t)j * 4 + q) * V + site];
-                m.e[2 * q] = make_float2(v.x, v.y);
-                m.e[2 * q + 1] = make_float2(v.z, v.w);
-            }
-            m.e[8] = b[(size_t)j * V + site];
-        } else if (C == BRI_LINK_2ROW) {
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                float4 v = a[((size_t)j * 3 + q) * V + site];
-                m.e[2 * q] = make_float2(v.x, v.y);
-                m.e[2 * q + 1] = make_float2(v.z, v.w);
-            }
-            third_row(m);
-        } else {
-            float4 v0 = a[((size_t)j * 2) * V + site], v1 = a[((size_t)j * 2 + 1) * V + site];
-            float p[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-            m = from_eight(p);
+        const float4 *p = chunk0(j, site);
+        if (C == BRI_LINK_8PARAM) {
+            float4 v0 = p[0], v1 = p[32];
+            float pr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            return from_eight(pr);
         }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            float4 v = p[32 * q];
+            m.e[2 * q] = make_float2(v.x, v.y);
+            m.e[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        if (C == BRI_LINK_FULL) m.e[8] = b[(size_t)j * VP + site];
+        else third_row(m);
         return m;
     }
 };
@@ -181,31 +182,34 @@ template <bri_comp C> struct LinkF32 {
 template <bri_comp C> struct LinkF16 {
     using T = float2;
     static constexpr int SLOTS = C == BRI_LINK_FULL ? 3 : C == BRI_LINK_2ROW ? 2 : 1;
+    static constexpr int NQ = C == BRI_LINK_FULL ? 2 : 1;  // uint4 chunks
     const uint4 *__restrict__ a;
     const void *__restrict__ b;
-    int V;
+    int VP;  // sites per field, V rounded up to a multiple of 32
+    BRI_D const uint4 *chunk0(int j, int s) const {
+        return a + ((size_t)j * VP + (s & ~31)) * NQ + (s & 31);
+    }
     BRI_D void prefetch(int j, int site, uint32_t dst, uint32_t stride) const {
+        const uint4 *p = chunk0(j, site);
         if (C == BRI_LINK_FULL) {
-            cp_async16(dst, a + ((size_t)j * 2) * V + site);
-            cp_async16(dst + stride, a + ((size_t)j * 2 + 1) * V + site);
-            cp_async4(dst + 2 * stride, (const uint32_t *)b + (size_t)j * V + site);
+            cp_async16(dst, p);
+            cp_async16(dst + stride, p + 32);
+            cp_async4(dst + 2 * stride, (const uint32_t *)b + (size_t)j * VP + site);
         } else if (C == BRI_LINK_2ROW) {
-            cp_async16(dst, a + (size_t)j * V + site);
-            cp_async8(dst + stride, (const uint2 *)b + (size_t)j * V + site);
+            cp_async16(dst, p);
+            cp_async8(dst + stride, (const uint2 *)b + (size_t)j * VP + site);
         } else {
-            cp_async16(dst, a + (size_t)j * V + site);
+            cp_async16(dst, p);
         }
     }
     BRI_D void prefetch_field_l2(int j, int site) const {
+        const uint4 *p = chunk0(j, site);
+        prefetch_l2(p);
         if (C == BRI_LINK_FULL) {
-            prefetch_l2(a + ((size_t)j * 2) * V + site);
-            prefetch_l2(a + ((size_t)j * 2 + 1) * V + site);
-            prefetch_l2((const uint32_t *)b + (size_t)j * V + site);
+            prefetch_l2(p + 32);
+            prefetch_l2((const uint32_t *)b + (size_t)j * VP + site);
         } else if (C == BRI_LINK_2ROW) {
-            prefetch_l2(a + (size_t)j * V + site);
-            prefetch_l2((const uint2 *)b + (size_t)j * V + site);
-        } else {
-            prefetch_l2(a + (size_t)j * V + site);
+            prefetch_l2((const uint2 *)b + (size_t)j * VP + site);
         }
     }
     BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
@@ -230,27 +234,28 @@ template <bri_comp C> struct LinkF16 {
     }
     BRI_D M3<float2> load(int j, int site) const {
         M3<float2> m;
+        const uint4 *p = chunk0(j, site);
         if (C == BRI_LINK_FULL) {
 #pragma unroll
             for (int q = 0; q < 2; q++) {
-                uint4 v = a[((size_t)j * 2 + q) * V + site];
+                uint4 v = p[32 * q];
                 m.e[4 * q] = h2f(v.x);
                 m.e[4 * q + 1] = h2f(v.y);
                 m.e[4 * q + 2] = h2f(v.z);
                 m.e[4 * q + 3] = h2f(v.w);
             }
-            m.e[8] = h2f(((const uint32_t *)b)[(size_t)j * V + site]);
+            m.e[8] = h2f(((const uint32_t *)b)[(size_t)j * VP + site]);
         } else if (C == BRI_LINK_2ROW) {
-            uint4 v = a[(size_t)j * V + site];
-            uint2 t = ((const uint2 *)b)[(size_t)j * V + site];
+            uint4 v = p[0];
+            uint2 t = ((const uint2 *)b)[(size_t)j * VP + site];
             m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
             m.e[4] = h2f(t.x); m.e[5] = h2f(t.y);
             third_row(m);
         } else {
-            uint4 v = a[(size_t)j * V + site];
+            uint4 v = p[0];
             float2 q0 = h2f(v.x), q1 = h2f(v.y), q2 = h2f(v.z), q3 = h2f(v.w);
-            float p[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
-            m = from_eight(p);
+            float pr[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
+            m = from_eight(pr);
         }
         return m;
     }
