@@ -187,6 +187,7 @@ template <bri_comp C> struct LinkF16 {
     const void *__restrict__ b;
     int VP;  // sites per field, V rounded up to a multiple of 32
     BRI_D const uint4 *chunk0(int j, int s) const {
+        if (NQ == 1) return a + (size_t)j * VP + s;  // one chunk: plain [40][Vp]
         return a + ((size_t)j * VP + (s & ~31)) * NQ + (s & 31);
     }
     BRI_D void prefetch(int j, int site, uint32_t dst, uint32_t stride) const {
