@@ -83,8 +83,9 @@ BRI_D float2 f2(float v) { return make_float2(v, v); }
 // FP32 hop with packed FMAs, chi = W psi as sum_c' (psi.re * w + psi.im * (i w)),
 // with the offset d a runtime value: the FP32 kernels loop over the 40 (d, -d)
 // pairs instead of unrolling them, which keeps the kernel small enough for the
-// instruction cache (the unrolled form stalls on instruction fetch).  The gamma terms are taken under warp-uniform branches
-// on d_mu, so no arithmetic is wasted; the spin permutations stay compile-time.
+// instruction cache (the unrolled form stalls on instruction fetch).  The gamma
+// terms are taken under warp-uniform branches on d_mu, so no arithmetic is
+// wasted; the spin permutations stay compile-time.
 template <int SGN>
 BRI_D void hop_body(const M3<float2> &W, const float2 p[12], float l, float r, const int dm[4], AccF &acc) {
     float2 A[9], B[9];
