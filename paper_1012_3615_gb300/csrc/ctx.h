@@ -83,6 +83,7 @@ struct DevBuf {
 // entry points implemented in the individual translation units
 bri_status bri_hops_build_impl(bri_ctx *ctx, cudaStream_t s);
 bri_status bri_hops_store_impl(bri_ctx *ctx, bri_prec prec, bri_comp comp, cudaStream_t s);
+bri_status bri_pair_store_impl(bri_ctx *ctx, bri_prec prec, cudaStream_t s);
 bri_status bri_project_impl(bri_ctx *ctx, double2 *Y, const double2 *A, long n, cudaStream_t s);
 // dslash: out = D in (mode 0), D^dagger in (mode 1), gamma5 (D - rho) in (mode 2, m0 = -rho)
 bri_status bri_dslash_impl(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode,

@@ -81,6 +81,8 @@ static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void
         const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
         if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
         const LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
+        if ((threads >> 11) == 3 && !ps.valid && !g.clov64 && g.s0 == 0 && g.s1 == g.V)
+            BRI_RETURN_IF(bri_pair_store_impl(ctx, prec, s));  // first use of the site-pair kernel
         if ((threads >> 11) == 3 && ps.valid && !g.clov64 && g.s0 == 0 && g.s1 == g.V) {
             // site-pair kernel on the interleaved copy
             const int thr = (threads & 2047) ? (threads & 2047) : 64;

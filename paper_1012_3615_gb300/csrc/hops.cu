@@ -267,28 +267,39 @@ bri_status bri_hops_store_impl(bri_ctx *ctx, bri_prec prec, bri_comp comp, cudaS
     }
     BRI_LAUNCHED(ctx);
     st.valid = true;
-    // site-pair interleaved copy for the pair kernel (full and 2-row, even t extent)
+    // the site-pair copy follows on first use of its launch variant
+    (prec == BRI_F32 ? ctx->p32 : ctx->p16).valid = false;
+    return BRI_OK;
+}
+
+// site-pair interleaved copy of the stored fields for the pair kernel (full
+// and 2-row storage, even t extent), built from the FP64 fields when the pair
+// launch variant is first asked for
+bri_status bri_pair_store_impl(bri_ctx *ctx, bri_prec prec, cudaStream_t s) {
+    const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
     LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
+    const bri_comp comp = st.comp;
+    const size_t V = ctx->g.V;
+    const int T = 128;
     ps.valid = false;
-    if (comp != BRI_LINK_8PARAM && ctx->g.L[3] % 2 == 0) {
-        const int E = comp == BRI_LINK_FULL ? 9 : 6;
-        if (ps.a && ps.comp != comp) {
-            cudaFree(ps.a);
-            ps.a = nullptr;
-        }
-        if (!ps.a) BRI_TRY_CUDA(ctx, cudaMalloc(&ps.a, (prec == BRI_F32 ? 16 : 8) * (size_t)E * NCANON * (V / 2)));
-        ps.comp = comp;
-        dim3 pg((unsigned)((V / 2 + T - 1) / T), NCANON);
-        if (prec == BRI_F32) {
-            if (E == 9) k_store_pair_f32<9><<<pg, T, 0, s>>>(ctx->hops64, (float4 *)ps.a, ctx->g);
-            else k_store_pair_f32<6><<<pg, T, 0, s>>>(ctx->hops64, (float4 *)ps.a, ctx->g);
-        } else {
-            if (E == 9) k_store_pair_f16<9><<<pg, T, 0, s>>>(ctx->hops64, (uint2 *)ps.a, ctx->g);
-            else k_store_pair_f16<6><<<pg, T, 0, s>>>(ctx->hops64, (uint2 *)ps.a, ctx->g);
-        }
-        BRI_LAUNCHED(ctx);
-        ps.valid = true;
+    if (!ctx->have64 || comp == BRI_LINK_8PARAM || ctx->g.L[3] % 2 != 0) return BRI_OK;
+    const int E = comp == BRI_LINK_FULL ? 9 : 6;
+    if (ps.a && ps.comp != comp) {
+        cudaFree(ps.a);
+        ps.a = nullptr;
     }
+    if (!ps.a) BRI_TRY_CUDA(ctx, cudaMalloc(&ps.a, (prec == BRI_F32 ? 16 : 8) * (size_t)E * NCANON * (V / 2)));
+    ps.comp = comp;
+    dim3 pg((unsigned)((V / 2 + T - 1) / T), NCANON);
+    if (prec == BRI_F32) {
+        if (E == 9) k_store_pair_f32<9><<<pg, T, 0, s>>>(ctx->hops64, (float4 *)ps.a, ctx->g);
+        else k_store_pair_f32<6><<<pg, T, 0, s>>>(ctx->hops64, (float4 *)ps.a, ctx->g);
+    } else {
+        if (E == 9) k_store_pair_f16<9><<<pg, T, 0, s>>>(ctx->hops64, (uint2 *)ps.a, ctx->g);
+        else k_store_pair_f16<6><<<pg, T, 0, s>>>(ctx->hops64, (uint2 *)ps.a, ctx->g);
+    }
+    BRI_LAUNCHED(ctx);
+    ps.valid = true;
     return BRI_OK;
 }
 
