@@ -346,7 +346,8 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * the L2 link-prefetch variant of the plain FP32 kernel, adding 4096
  * the cp.async shared-memory link-prefetch variant (at most 256 threads),
  * adding 6144 the site-pair kernel (two sites per thread, full and 2-row
- * storage with an even t extent; otherwise the plain kernel), adding 8192 the
+ * storage with an even t extent, its interleaved copy of the fields built on
+ * first use; otherwise the plain kernel), adding 8192 the
  * plain kernel without the separate accumulator for the +-i gamma entries,
  * adding 10240 the L2 link-prefetch kernel that combines the hops d and -d
  * before their gamma terms, adding 12288 that kernel held to 128 registers,
@@ -354,7 +355,9 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * bri_get_threads returns the current choice or a negative bri_status;
  * untuned, 128 threads with: the unrolled kernel (BRI_F64); variant 10240
  * (FP32 full, FP16 2-row fields); 14336 (FP32 2-row, FP16 full fields);
- * 12288 (8-parameter fields). */
+ * 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for
+ * nrhs < 1, a negative value, 1..31 or more than 1024 threads, or a variant
+ * above 14336. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 
