@@ -11,7 +11,12 @@ site) x V / time; the hopping fields alone are ~6 GB, far above L2, so no
 flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f32-full]
-                    [--nrhs 1] [--impl native|reference] [--sweep] [--solve]
+                    [--nrhs 1] [--impl native|reference] [--sweep] [--no-solve]
+
+The default line also carries the solver half of the metric ("solve"): time to
+a true FP64 relative residual of 1e-10 on 16^3x32 (FP64 BiCGstab vs FP64
+defect correction around FP32 BiCGstab) and on 24^3x48 (12 point sources
+solved together vs FP64 one after the other).
 """
 import argparse
 import json
@@ -33,10 +38,28 @@ LINK_BYTES = {  # bytes per site of the 40 stored hopping fields
     "f64-full": 40 * 144, "f32-full": 40 * 72, "f32-2row": 40 * 48, "f32-8param": 40 * 32,
     "f16-full": 40 * 36, "f16-2row": 40 * 24, "f16-8param": 40 * 16,
 }
-FLOPS_PER_SITE = 34032  # per right-hand side: 80 hops x 4 spins x 3 rows x 3 complex MACs (8 flops)
-                        # + per (d, -d) pair of class n: sum and difference of the two colour
-                        # products (2 x 24 real FMAs), lambda term (24), gamma terms (24 n),
-                        # + diagonal (24); FMA = 2 flops
+# Algorithmic flops per site and right-hand side, the method's count:
+#   80 hops x 4 spins x one 3x3 complex mat-vec (9 complex multiplies x 6 +
+#   6 complex adds x 2 = 66 flops)                                  = 21,120
+#   + 24 (1 + n) real adds per hop of class n into the lambda and the
+#   n gamma_mu accumulators of its class (sum over the 80 hops)     =  7,104
+#   + class scaling (4 classes x 5 accumulators x 24 multiplies)    =    480
+#   + summing the 4 classes (5 accumulators x 3 x 24 adds)          =    360
+#   + gamma combine (4 x 24 adds) and the diagonal (24 x 2)         =    144
+#                                                                   = 29,208
+# plus 42 flops per use of a 2-row field (third row = conj(r0 x r1), 80 uses).
+# The 8-parameter decoders are not counted (their cost is the format's).
+FLOPS_PER_SITE = 29208
+FLOPS_2ROW = 80 * 42
+# what the kernels execute: 80 hops x 4 spins x 9 complex MACs as 8 flops
+# each, + per (d, -d) pair of class n the sum and difference of the two colour
+# products (2 x 24 FMAs), the lambda term (24) and the gamma terms (24 n), +
+# the diagonal (24); FMA = 2 flops
+IMPL_FLOPS_PER_SITE = 34032
+
+
+def method_flops(mode):
+    return FLOPS_PER_SITE + (FLOPS_2ROW if mode.endswith("2row") else 0)
 
 
 def spinor_bytes(mode):
@@ -49,7 +72,15 @@ def site_bytes(mode, nrhs):
 
 KERNEL_SOURCES = ["paper_1012_3615_gb300/csrc/dslash_kernel.cuh", "paper_1012_3615_gb300/csrc/dslash_pair.cuh",
                   "paper_1012_3615_gb300/csrc/links.cuh", "paper_1012_3615_gb300/csrc/common.cuh"]
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x (FMA = 2) x max SM clock
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x (FMA = 2) x max SM clock
+
+
+def alu_peaks():
+    """FP32 (packed FMA) and FP64 FMA peaks of this GPU, measured by the
+    library's own microbenchmark (bri_alu_peak) at the clocks it runs at"""
+    from paper_1012_3615_gb300.core import alu_peak
+
+    return {"f32": alu_peak("f32"), "f64": alu_peak("f64")}
 
 
 def kernel_hash():
@@ -345,7 +376,10 @@ def native(args, world, rank, local, pg):
            "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
            "d2h_bytes_per_step": int(oh.numel() * oh.element_size()), "ms_per_step": e2e_s * 1e3}
 
-    flops = FLOPS_PER_SITE * nrhs * V / (ms * 1e-3) / 1e12
+    flops = method_flops(mode) * nrhs * V / (ms * 1e-3) / 1e12
+    impl_flops = IMPL_FLOPS_PER_SITE * nrhs * V / (ms * 1e-3) / 1e12
+    peaks = alu_peaks()
+    alu_peak_v = peaks["f64"] if prec == "f64" else peaks["f32"]
     line = {
         "metric": "D_B apply GB/s", "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -360,10 +394,13 @@ def native(args, world, rank, local, pg):
                      "traffic": measured_traffic(mode, nrhs, op.threads(prec, nrhs), L),
                      "peak_kind": peak_kind + " hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": bytes_step, "tflops": flops,
-                     "alu": {"achieved_tflops": flops, "peak_tflops": FP32_PEAK_TFLOPS if prec != "f64" else 1.25,
-                             "frac": flops / (FP32_PEAK_TFLOPS if prec != "f64" else 1.25),
-                             "peak_kind": "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec != "f64"
-                             else "FP64 nominal 1.25 TFLOP/s"},
+                     "alu": {"achieved_tflops": flops, "flops_per_site": method_flops(mode),
+                             "peak_tflops": alu_peak_v, "frac": flops / alu_peak_v,
+                             "peak_kind": "measured (bri_alu_peak: %s FMA chains on every SM)"
+                                          % ("FP64" if prec == "f64" else "packed FP32"),
+                             "impl_tflops": impl_flops, "impl_flops_per_site": IMPL_FLOPS_PER_SITE,
+                             "impl_frac": impl_flops / alu_peak_v,
+                             "measured_peaks_tflops": peaks, "fp32_nominal_tflops": FP32_NOMINAL_TFLOPS},
                      "kernel_hash": kernel_hash()},
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -388,12 +425,13 @@ def native(args, world, rank, local, pg):
                     op.tune(p, nr)
                 t = time_apply(op, xx, oo, m, nr, 3 if p == "f64" else 10, 2, stream)
                 b = site_bytes(m, nr) * V
-                sweep["%s/n%d" % (m, nr)] = {"ms": t, "GB/s": b / (t * 1e-3) / 1e9,
+                sweep["%s/n%d" % (m, nr)] = {"ms": t, "ms_per_rhs": t / nr, "GB/s": b / (t * 1e-3) / 1e9,
                                              "frac_hbm": b / (t * 1e-3) / 1e9 / peak,
-                                             "TFLOP/s": FLOPS_PER_SITE * nr * V / (t * 1e-3) / 1e12}
+                                             "TFLOP/s": method_flops(m) * nr * V / (t * 1e-3) / 1e12}
                 del xx, oo
         line["sweep"] = sweep
-    if args.solve:
+    if not args.no_solve and world == 1:
+        del x, out
         torch.cuda.empty_cache()
         line["solve"] = solve_bench(args, dev)
     if args.rows:
@@ -442,7 +480,7 @@ def rows_bench(dev):
             op.apply(psi, 0.0, out=o)
             ms, _ = timed(lambda: op.apply(psi, 0.0, out=o), reps=10)
             out["apply_fp64_8x8x8x8"] = {"ms": ms, "GB/s": site_bytes("f64-full", 1) * V / (ms * 1e-3) / 1e9,
-                                          "TFLOP/s": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e12}
+                                          "TFLOP/s": method_flops("f64-full") * V / (ms * 1e-3) / 1e12}
         del op, U
         torch.cuda.empty_cache()
     L = (12, 12, 12, 12)
@@ -471,39 +509,54 @@ def rows_bench(dev):
 
 
 def solve_bench(args, dev):
-    """Solver workloads: time to a true FP64 residual of 1e-10 (each timed solve
-    after one untimed solve of the same shape, which sets up work spaces and
-    CUDA graphs).
-    A: 16^3x32, m0 = -0.05, links exp(i0.4H), Z2 source, hops FP32 2-row / FP16 2-row:
-       FP64 BiCGstab vs mixed defect correction (FP32 and FP16 inner).
-    B: 24^3x48, m0 = 0, links exp(i0.35H), 12 spin-colour point sources at one site,
-       FP16 2-row hops: one batched solve of all 12 vs 12 sequential mixed (FP16) solves,
-       and the FP64 time of the first source."""
+    """Solver workloads: time to a true FP64 relative residual of 1e-10, each
+    timed solve after an untimed one of the same shape cut short (maxit 20),
+    which sets up the work spaces and captures the CUDA graphs; nvidia-smi
+    clocks are sampled during each workload.
+    A: 16^3x32, m0 = -0.05, links exp(i0.4H), Z2 source, hopping fields in FP32
+       2-row form (and FP16 2-row): FP64 BiCGstab vs FP64 defect correction
+       around FP32 BiCGstab (FP32 and FP16 fields).
+    B: 24^3x48, m0 = 0, links exp(i0.35H), the 12 spin-colour point sources at
+       one random site: batched defect correction of all 12 together (FP16
+       2-row fields, mode 3; FP32 2-row fields, mode 4) vs the FP64 solves of
+       the sources one after the other (the first --fp64-sources of them)."""
     import numpy as np
     import torch
 
     from paper_1012_3615_gb300 import Brillouin, synth
 
+    def run(op, b, m0, mode):
+        op.solve(b, m0=m0, tol=1e-10, maxit=20, mode=mode)  # warm-up: work spaces, CUDA graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = op.solve(b, m0=m0, tol=1e-10, maxit=20000, mode=mode)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return {"seconds": dt, "iters": [i["iters"] for i in info], "outer": [i["outer_iters"] for i in info],
+                "true_resid_max": max(i["true_resid"] for i in info),
+                "status": sorted(set(i["status"] for i in info))}
+
     out = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     L = (16, 16, 16, 32)
     U = synth.random_su3_links_torch(L, 0.4, SEED + 2, device=dev)
     op = Brillouin(L, BC)
     op.build_hops(U, prec="f32", comp="2row")
     op.store_hops("f16", "2row")
     b = torch.as_tensor(synth.z2_spinor(L, 1, SEED + 3), device=dev)
-    res = {}
+    res = {"workload": "16^3x32, m0=-0.05, links exp(i0.4H), Z2 source, hops FP32 2-row / FP16 2-row"}
     for mode, name in ((0, "fp64"), (1, "mixed_f32"), (2, "mixed_f16")):
-        op.solve(b, m0=-0.05, tol=1e-10, maxit=20000, mode=mode)  # warm-up: work spaces, CUDA graphs
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, info = op.solve(b, m0=-0.05, tol=1e-10, maxit=20000, mode=mode)
-        torch.cuda.synchronize()
-        res[name] = dict(info[0], seconds=time.perf_counter() - t0)
+        res[name] = run(op, b, -0.05, mode)
     res["speedup_mixed_f32_vs_fp64"] = res["fp64"]["seconds"] / res["mixed_f32"]["seconds"]
     res["speedup_mixed_f16_vs_fp64"] = res["fp64"]["seconds"] / res["mixed_f16"]["seconds"]
+    res["clocks"] = clocks.stop()
     out["solve_16x16x16x32"] = res
     del op, U
+    torch.cuda.empty_cache()
     if not args.solve_small:
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
         L = (24, 24, 24, 48)
         V = synth.volume(L)
         U = synth.random_su3_links_torch(L, 0.35, SEED + 4, device=dev)
@@ -514,41 +567,22 @@ def solve_bench(args, dev):
         for s_ in range(4):
             for c in range(3):
                 b[3 * s_ + c, x0, s_, c] = 1.0
-        res = {}
-        op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=3)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, info = op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=3)
-        torch.cuda.synchronize()
-        res["batched_12"] = {"seconds": time.perf_counter() - t0, "iters": [i["iters"] for i in info],
-                             "outer": [i["outer_iters"] for i in info],
-                             "true_resid_max": max(i["true_resid"] for i in info),
-                             "status": sorted(set(i["status"] for i in info))}
-        t0 = time.perf_counter()
-        xs, infs = op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=2)  # one after the other
-        torch.cuda.synchronize()
-        res["sequential_12_mixed_f16"] = {"seconds": time.perf_counter() - t0,
-                                          "true_resid_max": max(i["true_resid"] for i in infs)}
-        t0 = time.perf_counter()
-        x1, inf1 = op.solve(b[:1].contiguous(), m0=0.0, tol=1e-10, maxit=20000, mode=0)
-        torch.cuda.synchronize()
-        res["fp64_first_source"] = dict(inf1[0], seconds=time.perf_counter() - t0)
-        res["speedup_batched_vs_sequential_mixed"] = res["sequential_12_mixed_f16"]["seconds"] / res["batched_12"]["seconds"]
-        res["speedup_batched_vs_12x_fp64"] = 12 * res["fp64_first_source"]["seconds"] / res["batched_12"]["seconds"]
-        # the same batched solve with FP32 2-row fields as the inner precision (mode 4):
-        # the apply is ALU-bound, so FP32 fields cost about what FP16 ones do, and the
-        # FP32 inner solves need fewer defect-correction cycles (FP64 residual applies)
+        res = {"workload": "24^3x48, m0=0, links exp(i0.35H), 12 spin-colour point sources at site %d" % x0}
+        res["batched_12_f16_fields"] = run(op, b, 0.0, 3)
         op.store_hops("f32", "2row")
-        op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=4)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x4, info4 = op.solve(b, m0=0.0, tol=1e-10, maxit=20000, mode=4)
-        torch.cuda.synchronize()
-        res["batched_12_f32_fields"] = {"seconds": time.perf_counter() - t0, "iters": [i["iters"] for i in info4],
-                                        "outer": [i["outer_iters"] for i in info4],
-                                        "true_resid_max": max(i["true_resid"] for i in info4),
-                                        "status": sorted(set(i["status"] for i in info4))}
+        res["batched_12_f32_fields"] = run(op, b, 0.0, 4)
+        nf = max(1, min(12, args.fp64_sources))
+        res["fp64_sequential"] = run(op, b[:nf].contiguous(), 0.0, 0)
+        res["fp64_sequential"]["sources"] = nf
+        t64 = res["fp64_sequential"]["seconds"] * 12.0 / nf
+        res["fp64_12_sources_seconds"] = t64
+        res["fp64_12_sources_kind"] = "measured" if nf == 12 else "%d of 12 sources measured, scaled by 12/%d" % (nf, nf)
+        res["speedup_batched_f16_vs_fp64"] = t64 / res["batched_12_f16_fields"]["seconds"]
+        res["speedup_batched_f32_vs_fp64"] = t64 / res["batched_12_f32_fields"]["seconds"]
+        res["clocks"] = clocks.stop()
         out["solve_24x24x24x48_12_point_sources"] = res
+        del op, U
+        torch.cuda.empty_cache()
     return out
 
 
@@ -676,8 +710,10 @@ def main():
     ap.add_argument("--mode", default="f32-full", choices=sorted(LINK_BYTES))
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--sweep", action="store_true")
-    ap.add_argument("--solve", action="store_true", help="add the solver workloads (time to 1e-10)")
+    ap.add_argument("--no-solve", action="store_true", help="leave out the solver workloads (time to 1e-10)")
     ap.add_argument("--solve-small", action="store_true", help="only the 16^3x32 solver workload")
+    ap.add_argument("--fp64-sources", type=int, default=12,
+                    help="point sources of the 24^3x48 workload solved in FP64 for the comparison (1-12)")
     ap.add_argument("--rows", action="store_true", help="add hop precompute, FP64 apply and force timings")
     ap.add_argument("--study", action="store_true",
                     help="add the Wilson / Brillouin comparison (Sec. 7.4 spectra, overlap degree, solver iterations)")

@@ -186,15 +186,31 @@ bri_status bri_force(bri_ctx *ctx, double *dU, const double *chi, const double *
 bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double m0, double tol,
                              int maxit, bri_solve_info *info, void *stream);
 
+/* The quantity whose link derivative bri_force_inverse gives, with its
+ * derivatives (the pseudofermion action of the second adjoint quantity):
+ *   S = phi^dagger (D^dagger D)^{-1} phi = |Y|^2,  X = (D^dagger D)^{-1} phi,
+ *   Y = D X,  dS/dU = -2 d Re(Y^dagger D X)/dU  (convention of bri_force),
+ *   dS/dRe phi + i dS/dIm phi = 2 X.
+ * The two solves run as in bri_force_inverse (FP64 defect correction when
+ * FP32 fields are stored, else FP64 BiCGstab) to the true relative residual
+ * tol.  S: host, 1 double (may be null);  X: device [V][4][3] complex128
+ * output (may be null);  dU: device [V][4][3][3] complex128, accumulated
+ * (+=; may be null);  phi: device [V][4][3] complex128.  info (host, may be
+ * null) receives the second solve's data.  Synchronises the stream.
+ * Errors: BRI_EINVAL (misaligned pointers, tol <= 0, maxit < 1), BRI_ESTATE
+ * (no fields built; dU with the clover term on), the solver's status. */
+bri_status bri_inverse_action(bri_ctx *ctx, double *S, double *X, double *dU, const double *phi, double m0,
+                              double tol, int maxit, bri_solve_info *info, void *stream);
+
 /* Batched SU(3) projection Y_i = P_SU(3)(A_i) (Eq. proj_SU), FP64.
  * A, Y: device, [n][3][3] complex128 (may alias).  Errors: BRI_EINVAL. */
 bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, void *stream);
 
-/* Hop precompute that allocates nothing, for callers that cannot allocate
- * device memory (an application whose own pool owns all device memory, an
- * embedding that must not grow its device footprint while running).  The
- * paper has no counterpart: it is the computation of bri_build_hops (path
- * sums of Sec. 5.1 and FP64 back-projection of Sec. 5.2) as a stateless call.
+/* Hop precompute that allocates nothing: the stateless, allocation-free form
+ * of bri_build_hops + bri_get_hops, for callers that cannot allocate device
+ * memory (an application whose own pool owns all device memory, an embedding
+ * that must not grow its device footprint while running).  The paper has no
+ * counterpart to this entry point.
  *   lat: the lattice, at most 4096 sites;  U: device, [V][4][3][3] complex128;
  *   W:   device output, [V][40][3][3] complex128, the layout of bri_get_hops.
  * The path sums live in a fixed scratch array inside the library (81 x 144
@@ -203,10 +219,20 @@ bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, voi
  * last call's contents (nothing needs to start at zero); calls that overlap
  * on the GPU race, so the caller serialises them.  The first call on a device
  * looks up the array's device address with that device current: make it
- * before any stream capture.  Errors (message via bri_last_error(NULL)):
- * BRI_EINVAL (null or misaligned pointers, extents < 3, bad bc_sign, more
- * than 4096 sites), BRI_ECUDA. */
+ * before any stream capture.  The address is looked up again after the
+ * device's context was destroyed and re-created (cudaDeviceReset).  Errors
+ * (message via bri_last_error(NULL)): BRI_EINVAL (null or misaligned
+ * pointers, extents < 3, bad bc_sign, more than 4096 sites), BRI_ECUDA. */
 bri_status bri_build_hops_noalloc(const bri_lattice *lat, const double *U, double *W, void *stream);
+
+/* Measured arithmetic peak of the current GPU in TFLOP/s (FMA = 2 flops):
+ * independent FMA chains on every SM timed with CUDA events, the fastest of
+ * five launches.  prec = BRI_F32: packed FP32 FMAs (fma.rn.f32x2, the form
+ * of the FP32 stencil); BRI_F64: FP64 FMAs.  These are the ALU rooflines the
+ * stencil's flop rate is compared with.  The paper has no counterpart.
+ * Synchronises the device's default stream.  Errors: BRI_EINVAL, BRI_ECUDA
+ * (message via bri_last_error(NULL)). */
+bri_status bri_alu_peak(int prec, double *tflops);
 
 /* result[0] + i result[1] = <a, b> = sum conj(a) b over nrhs spinor fields
  * (the dot product of the Krylov solvers, FP64 accumulation: per-block partial

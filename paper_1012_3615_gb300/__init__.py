@@ -12,14 +12,14 @@ only marshals torch tensors into it.
     out = op.apply(psi, m0=0.0)  # psi: cuda complex128 (V, 4, 3) or (n, V, 4, 3)
 """
 
-__all__ = ["Brillouin", "BriError", "DiracFunction"]
+__all__ = ["Brillouin", "BriError", "DiracFunction", "InverseActionFunction"]
 
 
 def __getattr__(name):
     if name in ("Brillouin", "BriError"):
         from . import core
         return getattr(core, name)
-    if name == "DiracFunction":
+    if name in ("DiracFunction", "InverseActionFunction"):
         from . import autograd
-        return autograd.DiracFunction
+        return getattr(autograd, name)
     raise AttributeError(name)

@@ -68,6 +68,8 @@ SIGNATURES = {
     "bri_force": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]),
     "bri_force_inverse": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                   ctypes.POINTER(bri_solve_info), c_void_p]),
+    "bri_inverse_action": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p, c_void_p, c_double,
+                                   c_double, c_int, ctypes.POINTER(bri_solve_info), c_void_p]),
     "bri_project_su3": (c_int, [c_void_p, c_void_p, c_void_p, c_long, c_void_p]),
     "bri_build_hops_noalloc": (c_int, [ctypes.POINTER(bri_lattice), c_void_p, c_void_p, c_void_p]),
     "bri_cdot": (c_int, [c_void_p, ctypes.POINTER(c_double), c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -87,6 +89,7 @@ SIGNATURES = {
     "bri_get_threads": (c_int, [c_void_p, c_int, c_int]),
     "bri_kernel_launches": (c_long, [c_void_p]),
     "bri_last_error": (ctypes.c_char_p, [c_void_p]),
+    "bri_alu_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
 }
 
 _lib = None

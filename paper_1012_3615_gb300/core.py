@@ -151,6 +151,19 @@ class Brillouin:
                                                ctypes.byref(info), _stream()))
         return dU, info.as_dict()
 
+    def inverse_action(self, phi, m0=0.0, tol=1e-12, maxit=20000, want_x=False, dU=None):
+        """S = phi^dagger (D^dagger D)^{-1} phi; returns (S, X or None, dU or
+        None, info) with X = (D^dagger D)^{-1} phi and dU += dS/dU when dU is
+        given (a zero tensor to obtain the force alone)."""
+        self._spinor(phi, "f64")
+        S = ctypes.c_double()
+        X = torch.empty_like(phi) if want_x else None
+        info = abi.bri_solve_info()
+        self._check(self.lib.bri_inverse_action(self.ctx, ctypes.byref(S), _ptr(X) if want_x else None,
+                                                _ptr(dU) if dU is not None else None, _ptr(phi), float(m0),
+                                                float(tol), int(maxit), ctypes.byref(info), _stream()))
+        return S.value, X, dU, info.as_dict()
+
     def cdot(self, a, b, prec="f64"):
         """<a, b> = sum conj(a) b (FP64 accumulation in the library)."""
         n = self._spinor(a, prec)
@@ -158,26 +171,6 @@ class Brillouin:
         r = (ctypes.c_double * 2)()
         self._check(self.lib.bri_cdot(self.ctx, r, _ptr(a), _ptr(b), n, _PREC[prec], _stream()))
         return complex(r[0], r[1])
-
-    def max_eig_ddag_d(self, iters=60, m0=0.0, prec="f32", seed=0):
-        """Largest eigenvalue of D^dagger D by power iteration (applies and dot
-        products in the library); returns the last Rayleigh quotient."""
-        g = torch.Generator(device="cuda")
-        g.manual_seed(seed)
-        dt = spinor_dtype(prec)
-        rdt = torch.float64 if dt == torch.complex128 else torch.float32
-        x = torch.complex(torch.randn((1, self.V, 4, 3), generator=g, device="cuda", dtype=rdt),
-                          torch.randn((1, self.V, 4, 3), generator=g, device="cuda", dtype=rdt))
-        y = torch.empty_like(x)
-        lam = 0.0
-        for _ in range(iters):
-            nx = self.cdot(x, x, prec).real ** 0.5
-            x = x / nx
-            self.apply(x, m0, prec=prec, out=y)
-            z = self.apply(y, m0, dagger=True, prec=prec)
-            lam = self.cdot(x, z, prec).real
-            x = z
-        return lam
 
     # ---- link smearing and the clover term (Eq. def_ape, Eq. def_pref) ---------------
     def ape_smear(self, U, alpha=0.72, nsteps=1, out=None):
@@ -261,6 +254,16 @@ class Brillouin:
 
     def kernel_launches(self):
         return int(self.lib.bri_kernel_launches(self.ctx))
+
+
+def alu_peak(prec="f32"):
+    """measured FMA peak of the current GPU in TFLOP/s (FP32 packed or FP64)"""
+    lib = abi.load()
+    v = ctypes.c_double()
+    st = lib.bri_alu_peak(_PREC[prec], ctypes.byref(v))
+    if st != 0:
+        raise BriError(st, lib.bri_last_error(None).decode())
+    return v.value
 
 
 def build_hops_noalloc(L, bc, U, out=None):

@@ -214,14 +214,10 @@ bri_status bri_force(bri_ctx *ctx, double *dU, const double *chi, const double *
     return bri_force_impl(ctx, (double2 *)dU, (const double2 *)chi, (const double2 *)psi, as_stream(stream));
 }
 
-bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double m0, double tol, int maxit,
-                             bri_solve_info *info, void *stream) {
-    if (!ctx) return BRI_EINVAL;
-    if (!dU || !phi || !bri_aligned16(dU) || !bri_aligned16(phi))
-        return bri_fail(ctx, BRI_EINVAL, "dU and phi must be 16-byte aligned device pointers");
-    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
-    if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "the force of the clover term is not built (csw must be 0)");
-    cudaStream_t s = as_stream(stream);
+// S = phi^dagger (D^dagger D)^{-1} phi = |Y|^2 with X = (D^dagger D)^{-1} phi,
+// Y = D X; optionally X itself and dU += dS/dU = -2 d Re(Y^dagger D X)/dU.
+static bri_status inverse_action(bri_ctx *ctx, double *S, double *Xout, double *dU, const double *phi, double m0,
+                                 double tol, int maxit, bri_solve_info *info, cudaStream_t s) {
     const size_t n = (size_t)ctx->g.V * 12, bytes = n * sizeof(double2);
     DevBuf work;
     BRI_TRY_CUDA(ctx, cudaMalloc(&work.p, 4 * bytes));
@@ -240,14 +236,44 @@ bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double
         BRI_TRY_CUDA(ctx, cudaMemsetAsync(X, 0, bytes, s));
         if ((st = bri_solve_impl(ctx, (double *)X, (const double *)t, 1, m0, tol, maxit, mode, &i2, s)) != BRI_OK) break;
         if ((st = bri_dslash_impl(ctx, Y, X, 1, m0, 0, BRI_F64, s)) != BRI_OK) break;
-        // -2 d Re(Y^dagger D X)/dU: scale Y by -2
-        if ((st = gamma5_scale(ctx, t, Y, 0, -2.0, s)) != BRI_OK) break;
-        st = bri_force_impl(ctx, (double2 *)dU, t, X, s);
+        if (S) {
+            double r[2];
+            if ((st = bri_cdot_impl(ctx, r, Y, Y, n, BRI_F64, s)) != BRI_OK) break;
+            *S = r[0];
+        }
+        if (Xout) BRI_TRY_CUDA(ctx, cudaMemcpyAsync(Xout, X, bytes, cudaMemcpyDeviceToDevice, s));
+        if (dU) {
+            // -2 d Re(Y^dagger D X)/dU: scale Y by -2
+            if ((st = gamma5_scale(ctx, t, Y, 0, -2.0, s)) != BRI_OK) break;
+            st = bri_force_impl(ctx, (double2 *)dU, t, X, s);
+        }
     } while (0);
     cudaStreamSynchronize(s);
     if (info) *info = i2;
     if (st == BRI_OK && (i1.status != BRI_OK || i2.status != BRI_OK)) st = i1.status != BRI_OK ? i1.status : i2.status;
     return st;
+}
+
+bri_status bri_force_inverse(bri_ctx *ctx, double *dU, const double *phi, double m0, double tol, int maxit,
+                             bri_solve_info *info, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!dU || !phi || !bri_aligned16(dU) || !bri_aligned16(phi))
+        return bri_fail(ctx, BRI_EINVAL, "dU and phi must be 16-byte aligned device pointers");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "the force of the clover term is not built (csw must be 0)");
+    return inverse_action(ctx, nullptr, nullptr, dU, phi, m0, tol, maxit, info, as_stream(stream));
+}
+
+bri_status bri_inverse_action(bri_ctx *ctx, double *S, double *X, double *dU, const double *phi, double m0,
+                              double tol, int maxit, bri_solve_info *info, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!phi || !bri_aligned16(phi) || (X && !bri_aligned16(X)) || (dU && !bri_aligned16(dU)))
+        return bri_fail(ctx, BRI_EINVAL, "phi, X and dU must be 16-byte aligned device pointers");
+    if (!(tol > 0) || maxit < 1) return bri_fail(ctx, BRI_EINVAL, "tol must be > 0 and maxit >= 1");
+    if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "no hopping fields built");
+    if (dU && ctx->csw != 0.0)
+        return bri_fail(ctx, BRI_ESTATE, "the force of the clover term is not built (csw must be 0)");
+    return inverse_action(ctx, S, X, dU, phi, m0, tol, maxit, info, as_stream(stream));
 }
 
 bri_status bri_project_su3(bri_ctx *ctx, double *Y, const double *A, long n, void *stream) {

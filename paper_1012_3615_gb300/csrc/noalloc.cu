@@ -17,7 +17,12 @@
 //    reads before reading it (level n is written before level n+1 reads it).
 //  - the first call on a device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//    before any stream capture.  The address is cached per device together
+//    with the identity of the device's current context, and looked up again
+//    when the context changes (a cudaDeviceReset destroys the primary context
+//    and the module holding the array is loaded anew, possibly elsewhere).
+#include <cudaTypedefs.h>
+
 #include <cstring>
 #include <string>
 
@@ -36,6 +41,32 @@ namespace {
 
 void *g_scratch_addr[BRI_NOALLOC_MAX_DEVICES];
 bool g_scratch_ready[BRI_NOALLOC_MAX_DEVICES];
+unsigned long long g_scratch_ctx[BRI_NOALLOC_MAX_DEVICES];  // context id the address belongs to
+
+// unique id of the context current on this thread (0 if it cannot be read);
+// the driver calls are reached through the runtime, so the library does not
+// link against the driver library itself
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_current = (PFN_cuCtxGetCurrent_v4000)f1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)f2;
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // offsets of hop class n, packed class after class
 struct ClassList {
@@ -109,12 +140,17 @@ extern "C" bri_status bri_build_hops_noalloc(const bri_lattice *lat, const doubl
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= BRI_NOALLOC_MAX_DEVICES)
         return fail(BRI_ECUDA, "bri_build_hops_noalloc: no usable current device");
-    if (!g_scratch_ready[dev]) {
+    // make the device's primary context current (initialising it if needed)
+    // so that its identity can be compared with the cached one
+    if (cudaSetDevice(dev) != cudaSuccess) return fail(BRI_ECUDA, "bri_build_hops_noalloc: cudaSetDevice failed");
+    const unsigned long long ctx_id = current_context_id();
+    if (!g_scratch_ready[dev] || ctx_id == 0 || ctx_id != g_scratch_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_hop_scratch);
         if (e != cudaSuccess || !p)
             return fail(BRI_ECUDA, std::string("bri_build_hops_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx_id;
         g_scratch_ready[dev] = true;
     }
     M3<double2> *A = (M3<double2> *)g_scratch_addr[dev];

@@ -59,3 +59,18 @@ def test_python_binding_names_match_abi():
 
     for n in _declared():
         assert n in abi.SIGNATURES
+
+
+def test_noalloc_validates_pointers_without_gpu(lib):
+    """bri_build_hops_noalloc rejects null and misaligned pointers before any
+    CUDA call (the pointer values below are never dereferenced)."""
+    from paper_1012_3615_gb300 import abi
+
+    lat = abi.bri_lattice((ctypes.c_int * 4)(4, 4, 4, 4), (ctypes.c_int * 4)(1, 1, 1, -1))
+    assert lib.bri_build_hops_noalloc(None, 256, 512, None) == abi.BRI_EINVAL
+    assert lib.bri_build_hops_noalloc(ctypes.byref(lat), None, 512, None) == abi.BRI_EINVAL
+    assert lib.bri_build_hops_noalloc(ctypes.byref(lat), 256, None, None) == abi.BRI_EINVAL
+    assert b"null" in lib.bri_last_error(None)
+    assert lib.bri_build_hops_noalloc(ctypes.byref(lat), 256, 520, None) == abi.BRI_EINVAL
+    assert lib.bri_build_hops_noalloc(ctypes.byref(lat), 264, 512, None) == abi.BRI_EINVAL
+    assert b"aligned" in lib.bri_last_error(None)

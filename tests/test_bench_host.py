@@ -44,9 +44,20 @@ def test_measured_traffic_scales_by_sites_and_checks_the_hash(tmp_path, monkeypa
 
 
 def test_flop_count_of_one_apply():
-    # class sizes 8/24/32/16 hops = 4/12/16/8 (d, -d) pairs with n = 1..4 nonzero components
+    """The method's count (one mat-vec per hop and spin, accumulation into the
+    class accumulators, class scaling, gamma combine, diagonal) from the offsets
+    of the 3^4 hypercube, and the implementation's pair-form count."""
+    import itertools
+
+    classes = [sum(1 for c in d if c) for d in itertools.product((-1, 0, 1), repeat=4) if any(d)]
+    assert sorted(set(classes)) == [1, 2, 3, 4] and len(classes) == 80
+    matvec = 80 * 4 * (9 * 6 + 6 * 2)                         # 3x3 complex mat-vec per spin
+    accumulate = sum(24 * (1 + n) for n in classes)           # lambda + n gamma accumulators
+    scale, combine, gamma, diag = 4 * 5 * 24, 5 * 3 * 24, 4 * 24, 2 * 24
+    assert matvec + accumulate + scale + combine + gamma + diag == bench.FLOPS_PER_SITE == 29208
+    assert bench.method_flops("f32-2row") == 29208 + 80 * 42
+    # implementation: class sizes 8/24/32/16 hops = 4/12/16/8 (d, -d) pairs
     pairs = {1: 4, 2: 12, 3: 16, 4: 8}
     colour = 80 * 4 * 9 * 8                                  # complex MACs, 8 flops each
     spin = sum(k * 2 * (2 * 24 + 24 + 24 * n) for n, k in pairs.items())  # sum/difference, lambda, gamma
-    diag = 2 * 24
-    assert colour + spin + diag == bench.FLOPS_PER_SITE == 34032
+    assert colour + spin + 2 * 24 == bench.IMPL_FLOPS_PER_SITE == 34032

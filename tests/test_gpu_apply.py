@@ -1,6 +1,11 @@
 """GPU stencil apply (Eq. def_pref, class form of Sec. 8) against the CPU
-oracle: FP64 to 1e-13 relative, FP32 to 1e-6, per link storage format, for
-D, D^dagger and the overlap kernel gamma_5 (D - rho)."""
+oracle, element by element (max |gpu - ref| / max |ref|): FP64 to 1e-13,
+FP32 full and 2-row fields to 1e-6, for D, D^dagger and the overlap kernel
+gamma_5 (D - rho).  The lossy storage formats carry their own bounds
+(``TOL_MAX``): FP16 fields round every link entry to 11 bits, and the
+8-parameter form reconstructs |U00| and |U20| through square roots and
+divides by 1 - |U00|^2, both ill-conditioned near diagonal links, so its
+FP32 error is a property of the format, not of the arithmetic."""
 import numpy as np
 import pytest
 import torch
@@ -34,6 +39,17 @@ def _rel_l2(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+# per-element bounds (relative to max |ref|) per (precision, link format)
+TOL_MAX = {("f32", "full"): 1e-6, ("f32", "2row"): 1e-6, ("f32", "8param"): 5e-5,
+           ("f16", "full"): 3e-4, ("f16", "2row"): 3e-4, ("f16", "8param"): 1e-2}
+
+
+def _check(out, ref, tol, what=""):
+    """element-wise parity; the relative 2-norm is reported alongside"""
+    e = _rel_max(out, ref)
+    assert e < tol, (what, e, _rel_l2(out, ref))
+
+
 @pytest.mark.parametrize("L,bc", CASES)
 def test_fp64_apply_dagger_overlap(gpu, L, bc):
     U, psi, W = _setup(L, bc, sum(L))
@@ -50,9 +66,10 @@ def test_fp64_apply_dagger_overlap(gpu, L, bc):
         assert _rel_max(outh[r], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) < 1e-13
 
 
-@pytest.mark.parametrize("comp,tol", [("full", 1e-6), ("2row", 1e-6), ("8param", 2e-5)])
+@pytest.mark.parametrize("comp", ["full", "2row", "8param"])
 @pytest.mark.parametrize("L,bc", CASES[:2] + TILED)
-def test_fp32_apply(gpu, L, bc, comp, tol):
+def test_fp32_apply(gpu, L, bc, comp):
+    tol = TOL_MAX[("f32", comp)]
     U, psi, W = _setup(L, bc, 10 + sum(L))
     op = Brillouin(L, bc)
     op.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp=comp)
@@ -61,13 +78,14 @@ def test_fp32_apply(gpu, L, bc, comp, tol):
         out = op.apply(x, m0=0.02, dagger=dag, prec="f32").cpu().numpy()
         for r in range(psi.shape[0]):
             ref = oracle.apply(L, bc, W, 0.02, psi[r], dagger=dag)
-            assert _rel_l2(out[r], ref) < tol
+            _check(out[r], ref, tol, (dag, r))
     outh = op.overlap_kernel(x, rho=1.0, prec="f32").cpu().numpy()
-    assert _rel_l2(outh[0], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[0])) < tol
+    _check(outh[0], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[0]), tol, "overlap kernel")
 
 
-@pytest.mark.parametrize("comp,tol", [("full", 2e-3), ("2row", 2e-3), ("8param", 1e-2)])
-def test_fp16_links_apply(gpu, comp, tol):
+@pytest.mark.parametrize("comp", ["full", "2row", "8param"])
+def test_fp16_links_apply(gpu, comp):
+    tol = TOL_MAX[("f16", comp)]
     L, bc = (4, 4, 4, 6), AP
     U, psi, W = _setup(L, bc, 21)
     op = Brillouin(L, bc)
@@ -75,7 +93,7 @@ def test_fp16_links_apply(gpu, comp, tol):
     x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
     out = op.apply(x, m0=0.0, prec="f16").cpu().numpy()
     for r in range(psi.shape[0]):
-        assert _rel_l2(out[r], oracle.apply(L, bc, W, 0.0, psi[r])) < tol
+        _check(out[r], oracle.apply(L, bc, W, 0.0, psi[r]), tol, r)
 
 
 @pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f32", "2row"), ("f16", "2row")])
@@ -114,16 +132,16 @@ def test_kernel_variants_agree(gpu, prec, comp):
         op.set_threads(prec, 2, shape)
         outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
     for shape, o in outs[1:]:
-        err = (torch.linalg.vector_norm(o - outs[0][1]) / torch.linalg.vector_norm(outs[0][1])).item()
+        err = (torch.abs(o - outs[0][1]).max() / torch.abs(outs[0][1]).max()).item()
         assert err < 1e-6, (shape, err)
 
 
-@pytest.mark.parametrize("prec,comp,tol", [("f32", "full", 1e-6), ("f32", "2row", 1e-6), ("f16", "full", 2e-3),
-                                           ("f16", "2row", 2e-3)])
+@pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f32", "2row"), ("f16", "full"), ("f16", "2row")])
 @pytest.mark.parametrize("L,bc", [((3, 5, 4, 6), AP), ((4, 4, 4, 4), PER), ((8, 4, 4, 8), AP)])
-def test_pair_kernel_matches_oracle(gpu, prec, comp, tol, L, bc):
+def test_pair_kernel_matches_oracle(gpu, prec, comp, L, bc):
     """The site-pair kernel (two sites i, i + V/2 per thread, pair-interleaved
     links) against the oracle for D, D^dagger and the overlap kernel."""
+    tol = TOL_MAX[(prec, comp)]
     U, psi, W = _setup(L, bc, 50 + sum(L))
     op = Brillouin(L, bc)
     op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
@@ -134,17 +152,18 @@ def test_pair_kernel_matches_oracle(gpu, prec, comp, tol, L, bc):
         outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
         outh = op.overlap_kernel(x, rho=1.0, prec=prec).cpu().numpy()
         for r in range(psi.shape[0]):
-            assert _rel_l2(out[r], oracle.apply(L, bc, W, 0.05, psi[r])) < tol
-            assert _rel_l2(outd[r], oracle.apply(L, bc, W, 0.05, psi[r], dagger=True)) < tol
-            assert _rel_l2(outh[r], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) < tol
+            _check(out[r], oracle.apply(L, bc, W, 0.05, psi[r]), tol, (shape, "D"))
+            _check(outd[r], oracle.apply(L, bc, W, 0.05, psi[r], dagger=True), tol, (shape, "Ddag"))
+            _check(outh[r], oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r]), tol, (shape, "H"))
 
 
-@pytest.mark.parametrize("prec,comp,tol", [("f32", "full", 1e-6), ("f32", "8param", 1e-6), ("f16", "2row", 2e-3)])
+@pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f32", "2row"), ("f32", "8param"), ("f16", "2row")])
 @pytest.mark.parametrize("L,bc", [((3, 5, 4, 6), AP), ((4, 4, 4, 4), PER)])
-def test_pair_combined_body_matches_oracle(gpu, prec, comp, tol, L, bc):
+def test_pair_combined_body_matches_oracle(gpu, prec, comp, L, bc):
     """The loops that combine the hops d and -d before the gamma terms (launch
     variants 5-7) against the oracle for D, D^dagger and the overlap kernel, with
     the Brillouin and the Wilson weights."""
+    tol = TOL_MAX[(prec, comp)]
     U, psi, W = _setup(L, bc, 60 + sum(L))
     for name in ("brillouin", "wilson"):
         lam, rho = WEIGHTS[name]
@@ -164,9 +183,9 @@ def test_pair_combined_body_matches_oracle(gpu, prec, comp, tol, L, bc):
             outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
             outh = op.overlap_kernel(x, rho=1.0, prec=prec).cpu().numpy()
             for r in range(psi.shape[0]):
-                assert _rel_l2(out[r], ref[r][0]) < tol, (shape, name)
-                assert _rel_l2(outd[r], ref[r][1]) < tol, (shape, name)
-                assert _rel_l2(outh[r], ref[r][2]) < tol, (shape, name)
+                _check(out[r], ref[r][0], tol, (shape, name, "D"))
+                _check(outd[r], ref[r][1], tol, (shape, name, "Ddag"))
+                _check(outh[r], ref[r][2], tol, (shape, name, "H"))
 
 
 def test_multi_rhs_equals_single(gpu):
@@ -248,7 +267,7 @@ def test_full_size_sampled_sites(gpu):
     g64 = out64[0].cpu().numpy()[sites]
     g32 = out32[0].cpu().numpy()[sites]
     assert _rel_max(g64, ref) < 1e-13
-    assert _rel_l2(g32, ref) < 1e-6
+    _check(g32, ref, 1e-6, "32^3x64 FP32 sampled sites")
     del op
     torch.cuda.empty_cache()
 

@@ -71,3 +71,48 @@ def test_autograd_function(gpu):
     W = oracle.build_hops(L, Un)
     ref_psi = oracle.apply(L, AP, W, 0.05, chi.cpu().numpy(), dagger=True)
     assert np.abs(psi.grad.cpu().numpy() - ref_psi).max() <= 1e-12 * np.abs(ref_psi).max()
+
+
+def test_inverse_action_function(gpu):
+    """S = phi^dagger (D^dagger D)^{-1} phi through InverseActionFunction: S,
+    dS/dU and dS/dphi against the oracle's solves and force (1e-8 relative),
+    and dS/dU against central finite differences of S (eps = 1e-5) in single
+    link entries, real and imaginary parts."""
+    from paper_1012_3615_gb300 import InverseActionFunction
+
+    L, m0 = (4, 3, 3, 4), 0.1
+    Un = synth.random_su3_links(L, 0.3, 21)
+    phin = synth.gaussian_spinor(L, 1, 22)[0]
+    U = torch.as_tensor(Un, device=gpu).requires_grad_(True)
+    phi = torch.as_tensor(phin, device=gpu).requires_grad_(True)
+    op = Brillouin(L, AP)
+    S = InverseActionFunction.apply(U, phi, op, m0, 1e-13)
+    S.backward()
+    # oracle: D^dagger Z = phi (via gamma5), D X = Z, Y = D X
+    W = oracle.build_hops(L, Un)
+    g5 = np.diag([1, 1, -1, -1]).astype(complex)
+    w, _, _, _ = oracle.bicgstab(L, AP, W, m0, np.einsum("ab,xbc->xac", g5, phin), tol=1e-14)
+    X, _, _, _ = oracle.bicgstab(L, AP, W, m0, np.einsum("ab,xbc->xac", g5, w), tol=1e-14)
+    Y = oracle.apply(L, AP, W, m0, X)
+    S_ref = np.vdot(Y, Y).real
+    assert abs(S.item() - S_ref) <= 1e-10 * S_ref
+    ref_U = oracle.force(L, AP, Un, m0, -2 * Y, X)
+    assert np.abs(U.grad.cpu().numpy() - ref_U).max() <= 1e-8 * np.abs(ref_U).max()
+    assert np.abs(phi.grad.cpu().numpy() - 2 * X).max() <= 1e-8 * np.abs(2 * X).max()
+    # central differences of S in single entries of single links
+    rng = np.random.default_rng(23)
+    eps = 1e-5
+    G = U.grad.cpu().numpy()
+    V = synth.volume(L)
+    for _ in range(6):
+        x, mu, a, b = rng.integers(0, V), rng.integers(0, 4), rng.integers(0, 3), rng.integers(0, 3)
+        for part, unit in ((0, 1.0), (1, 1j)):
+            Sp = []
+            for sgn in (1, -1):
+                Up = Un.copy()
+                Up[x, mu, a, b] += sgn * eps * unit
+                Sp.append(InverseActionFunction.apply(torch.as_tensor(Up, device=gpu), phi.detach(), op, m0,
+                                                      1e-13).item())
+            fd = (Sp[0] - Sp[1]) / (2 * eps)
+            an = G[x, mu, a, b].real if part == 0 else G[x, mu, a, b].imag
+            assert abs(fd - an) <= 1e-6 * np.abs(G).max() + 1e-6 * abs(an), (x, mu, a, b, part, fd, an)

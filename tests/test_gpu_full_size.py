@@ -110,13 +110,16 @@ def test_storage_formats_and_rhs_32x32x32x64(gpu):
     sites = np.concatenate([[0, V - 1, 32 * 32 * 32 - 1], np.random.default_rng(7).integers(0, V, 5)])
     Uh = U.cpu().numpy()
     refs = [oracle.apply_sites(L, AP, Uh, 0.0, psi[r].cpu().numpy().astype(np.complex128), sites) for r in range(4)]
-    for prec, comp, tol in (("f32", "2row", 1e-6), ("f32", "8param", 1e-6), ("f16", "full", 2e-3),
-                            ("f16", "2row", 2e-3), ("f16", "8param", 2e-3)):
+    # per-element bounds relative to max |ref| over the sampled sites, one per
+    # (precision, link format): the lossy formats carry their own error
+    for prec, comp, tol in (("f32", "2row", 1e-6), ("f32", "8param", 5e-5), ("f16", "full", 3e-4),
+                            ("f16", "2row", 3e-4), ("f16", "8param", 1e-2)):
         op.store_hops(prec, comp)
         out = op.apply(psi, 0.0, prec=prec).cpu().numpy()
         for r in range(4):
             got = out[r][sites]
-            assert np.linalg.norm(got - refs[r]) <= tol * np.linalg.norm(refs[r]), (prec, comp, r)
+            err = np.abs(got - refs[r]).max() / np.abs(refs[r]).max()
+            assert err <= tol, (prec, comp, r, err)
     del op, U, psi
     torch.cuda.empty_cache()
 
@@ -140,7 +143,7 @@ def test_benchmark_workload_32x32x32x64(gpu):
     psi = x[0].cpu().numpy().astype(np.complex128)
     ref = oracle.apply_sites(L, AP, Uh, 0.0, psi, sites)
     got = out[0].cpu().numpy()[sites]
-    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
     del out
     x64 = x.to(torch.complex128)  # the FP64 fields stay next to the FP32 ones
     got64 = op.apply(x64, 0.0).cpu().numpy()[0][sites]

@@ -48,7 +48,7 @@ def test_clover_apply_matches_oracle(gpu, clover_case):
         o32 = op.apply(x32, 0.05, dagger=dag, prec="f32").cpu().numpy()
         for r in range(2):
             assert np.abs(o64[r] - ref[r]).max() <= 1e-13 * np.abs(ref[r]).max()
-            assert np.linalg.norm(o32[r] - ref[r]) <= 1e-6 * np.linalg.norm(ref[r])
+            assert np.abs(o32[r] - ref[r]).max() <= 1e-6 * np.abs(ref[r]).max()
     # the shifted hermitian kernel gamma5 (D - rho) includes the term too
     h = op.overlap_kernel(x64, 1.0).cpu().numpy()
     for r in range(2):

@@ -40,7 +40,7 @@ def test_weight_columns_match_oracle(gpu, oracle_weights, name):
         for r in range(2):
             ref = oracle.apply(L, AP, W, 0.03, psi[r], dagger=dag)
             assert np.abs(o64[r] - ref).max() <= 1e-13 * np.abs(ref).max()
-            assert np.linalg.norm(o32[r] - ref) <= 1e-6 * np.linalg.norm(ref)
+            assert np.abs(o32[r] - ref).max() <= 1e-6 * np.abs(ref).max()
     got = op.weights()
     assert np.allclose(got[0], lam) and np.allclose(got[1][1:], rho[1:])
 
@@ -95,6 +95,24 @@ def _free_max_symbol2(L, lam, rho):
     return float(np.max(lk ** 2 + s2))
 
 
+def _power_iteration(op, iters, m0, prec, seed=0):
+    """largest eigenvalue of D^dagger D: applies and dot products in the
+    library, the normalisation and the Rayleigh quotient here"""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    x = torch.complex(torch.randn((1, op.V, 4, 3), generator=g, device="cuda"),
+                      torch.randn((1, op.V, 4, 3), generator=g, device="cuda"))
+    y = torch.empty_like(x)
+    lam = 0.0
+    for _ in range(iters):
+        x = x / op.cdot(x, x, prec).real ** 0.5
+        op.apply(x, m0, prec=prec, out=y)
+        z = op.apply(y, m0, dagger=True, prec=prec)
+        lam = op.cdot(x, z, prec).real
+        x = z
+    return lam
+
+
 @pytest.mark.parametrize("name,expect", [("brillouin", 4.12), ("wilson", 64.0)])
 def test_free_field_largest_eigenvalue(gpu, name, expect):
     L = (8, 8, 8, 8)
@@ -102,7 +120,7 @@ def test_free_field_largest_eigenvalue(gpu, name, expect):
     op = Brillouin(L, (1, 1, 1, 1))
     op.set_weights(lam, rho)
     op.build_hops(torch.as_tensor(synth.unit_links(L), device=gpu), prec="f32", comp="full")
-    got = op.max_eig_ddag_d(iters=400, m0=0.0, prec="f32")
+    got = _power_iteration(op, 400, 0.0, "f32")
     exact = _free_max_symbol2(L, lam, rho)
     assert abs(exact - expect) < 0.01 * expect
     # the Rayleigh quotient approaches the top from below; the Brillouin
