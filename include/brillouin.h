@@ -377,13 +377,20 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * plain kernel without the separate accumulator for the +-i gamma entries,
  * adding 10240 the L2 link-prefetch kernel that combines the hops d and -d
  * before their gamma terms, adding 12288 that kernel held to 128 registers,
- * adding 14336 the same pair loop with the gamma terms after the spin loop.
+ * adding 14336 the same pair loop with the gamma terms after the spin loop,
+ * 16384 the tensor-core multi-RHS kernel (Sec. 8 class form as one complex
+ * (15 x 240) x (240 x 4 nrhs) product per site on mma.sync with FP16
+ * operands and FP32 accumulation; full link storage only, otherwise the
+ * untuned shape; accuracy that of FP16 operands, about 1e-4 of max |out|;
+ * the tuner considers it for BRI_F16 fields and nrhs >= 2 only, the accuracy
+ * class it shares).  For 16384 the low bits give the right-hand sides one
+ * warp takes per pass (an even number 2..12; 0 or anything else: 12).
  * bri_get_threads returns the current choice or a negative bri_status;
  * untuned, 128 threads with: the unrolled kernel (BRI_F64); variant 10240
  * (FP32 full, FP16 2-row fields); 14336 (FP32 2-row, FP16 full fields);
  * 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for
  * nrhs < 1, a negative value, 1..31 or more than 1024 threads, or a variant
- * above 14336. */
+ * above 16384. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 

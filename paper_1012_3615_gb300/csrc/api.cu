@@ -103,6 +103,8 @@ bri_status bri_destroy(bri_ctx *ctx) {
     bri_host_apply_free(ctx);
     cudaFree(ctx->clov64);
     cudaFree(ctx->clov32);
+    cudaFree(ctx->tc_amax);
+    cudaFree(ctx->tc_f);
     cudaFree(ctx->U);
     cudaFree(ctx->hops64);
     for (LinkStore *st : {&ctx->f32, &ctx->f16, &ctx->p32, &ctx->p16}) {
@@ -404,9 +406,10 @@ bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_prec(ctx, prec));
     const int thr = threads & 2047, variant = threads >> 11;
-    if (nrhs < 1 || threads < 0 || (thr > 0 && thr < 32) || thr > 1024 || variant > 7)
+    if (nrhs < 1 || threads < 0 || variant > 8 || (variant < 8 && ((thr > 0 && thr < 32) || thr > 1024)))
         return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
-    ctx->tune[bri_tune_key(ctx, prec, nrhs)] = (thr & ~31) | (variant << 11);
+    // variant 8 (tensor cores): the low bits are the right-hand sides per warp pass
+    ctx->tune[bri_tune_key(ctx, prec, nrhs)] = variant == 8 ? threads : (thr & ~31) | (variant << 11);
     return BRI_OK;
 }
 
@@ -440,8 +443,12 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     // candidates: tiled kernel (0), plain kernel at 64..512 threads, and the
     // variants of the FP32 plain kernel (launch shape above bit 11)
     for (int thr : {0, 64, 128, 256, 512, 128 | 2048, 128 | 4096, 256 | 4096, 64 | 6144, 128 | 6144, 128 | 8192,
-                    256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288, 128 | 14336}) {
+                    256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288, 128 | 14336,
+                    16384 | 4, 16384 | 6, 16384 | 8, 16384 | 12}) {
         if (thr == 0 && (prec == BRI_F64 || !tiled_ok(ctx->g))) continue;
+        // the tensor-core kernel has FP16-operand accuracy: a candidate for FP16
+        // fields (same accuracy class) with full storage only
+        if ((thr >> 11) == 8 && (prec != BRI_F16 || ctx->f16.comp != BRI_LINK_FULL || nrhs < 2)) continue;
         if ((thr >> 11) && prec == BRI_F64) continue;
         if ((st = bri_dslash_raw(ctx, out, in, nrhs, 0.0, 0, prec, nullptr, thr, s)) != BRI_OK) break;  // warm-up
         cudaEventRecord(e0, s);

@@ -240,4 +240,15 @@ template <int K, int SGN> BRI_D int nb_index(const SiteNb &n, int site, float &p
     return y;
 }
 
+// neighbour index and boundary phase of the forward (d) and reversed (-d) hop
+BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &phf, int &yb, float &phb) {
+    yf = yb = site;
+    phf = phb = 1.f;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (dm[mu] > 0) { yf += nb.fw[mu]; phf *= nb.sfw[mu]; yb += nb.bw[mu]; phb *= nb.sbw[mu]; }
+        else if (dm[mu] < 0) { yf += nb.bw[mu]; phf *= nb.sbw[mu]; yb += nb.fw[mu]; phb *= nb.sfw[mu]; }
+    }
+}
+
 }  // namespace bri

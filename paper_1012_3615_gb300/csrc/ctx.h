@@ -34,6 +34,9 @@ struct bri_ctx {
     double csw = 0.0;              // clover coefficient (0: no clover term)
     double2 *clov64 = nullptr;     // clover blocks, see Geom
     float4 *clov32 = nullptr;
+    unsigned *tc_amax = nullptr;   // per-RHS max |psi| of the tensor-core apply (65536 entries)
+    void *tc_f = nullptr;          // FP16 copy of the spinors for the tensor-core apply
+    size_t tc_fbytes = 0;
     long gen = 0;  // bumped whenever the operator changes (links, weights)
     std::map<std::string, int> tune;  // launch-shape cache: key -> threads per block
     std::string err;
@@ -89,6 +92,10 @@ bri_status bri_project_impl(bri_ctx *ctx, double2 *Y, const double2 *A, long n, 
 bri_status bri_dslash_impl(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode,
                            bri_prec prec, cudaStream_t s);
 bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s);
+// multi-RHS apply on the tensor cores (launch variant 8; FP32/FP16 full fields)
+// (cap: right-hand sides per warp pass, an even number 2..12; anything else: 12)
+bri_status bri_dslash_tc(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
+                         const int *skip, int cap, cudaStream_t s);
 // dslash with an explicit launch shape; skip[r] != 0 skips right-hand side r
 bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
                           const int *skip, int threads, cudaStream_t s);

@@ -80,6 +80,12 @@ static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void
     } else {
         const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
         if (!st.valid) return bri_fail(ctx, BRI_ESTATE, "hopping fields of this precision not built");
+        if ((threads >> 11) == 8) {
+            // tensor-core apply: full link storage, whole lattice, no clover term
+            if (st.comp == BRI_LINK_FULL && !g.clov64 && g.s0 == 0 && g.s1 == g.V)
+                return bri_dslash_tc(ctx, out, in, nrhs, m0, mode, prec, skip, threads & 2047, s);
+            threads = default_shape(ctx, prec);
+        }
         const LinkStore &ps = prec == BRI_F32 ? ctx->p32 : ctx->p16;
         if ((threads >> 11) == 3 && !ps.valid && !g.clov64 && g.s0 == 0 && g.s1 == g.V)
             BRI_RETURN_IF(bri_pair_store_impl(ctx, prec, s));  // first use of the site-pair kernel

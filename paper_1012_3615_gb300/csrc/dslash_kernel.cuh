@@ -305,17 +305,6 @@ BRI_D void pair_body_s(const float2 cf[12], const M3<float2> &W, const float2 p[
     }
 }
 
-// neighbour index and boundary phase of the forward (d) and reversed (-d) hop
-BRI_D void hop_nb(const int dm[4], int site, const SiteNb &nb, int &yf, float &phf, int &yb, float &phb) {
-    yf = yb = site;
-    phf = phb = 1.f;
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        if (dm[mu] > 0) { yf += nb.fw[mu]; phf *= nb.sfw[mu]; yb += nb.bw[mu]; phb *= nb.sbw[mu]; }
-        else if (dm[mu] < 0) { yf += nb.bw[mu]; phf *= nb.sbw[mu]; yb += nb.fw[mu]; phb *= nb.sfw[mu]; }
-    }
-}
-
 // FP32 stencil over the 40 (d, -d) pairs as a compact loop.  PF = true also
 // prefetches the two links of the next pair into L2 (the links stream from DRAM;
 // the neighbour spinors mostly hit L1/L2).

@@ -26,3 +26,12 @@ def gpu():
     abi.load()
     torch.cuda.set_device(0)
     return torch.device("cuda:0")
+
+
+@pytest.fixture
+def oracle_weights():
+    """set the oracle's class weights for one test (restored afterwards)"""
+    import oracle
+
+    yield oracle.set_weights
+    oracle.reset_weights()

@@ -15,12 +15,6 @@ pytestmark = pytest.mark.gpu
 AP = (1, 1, 1, -1)
 
 
-@pytest.fixture
-def oracle_weights():
-    yield oracle.set_weights
-    oracle.reset_weights()
-
-
 @pytest.mark.parametrize("name", ["wilson", "hypercube", "brillouin"])
 def test_weight_columns_match_oracle(gpu, oracle_weights, name):
     lam, rho = WEIGHTS[name]
