@@ -37,6 +37,8 @@ SEED = 1015
 LINK_BYTES = {  # bytes per site of the 40 stored hopping fields
     "f64-full": 40 * 144, "f32-full": 40 * 72, "f32-2row": 40 * 48, "f32-8param": 40 * 32,
     "f16-full": 40 * 36, "f16-2row": 40 * 24, "f16-8param": 40 * 16,
+    # FP16 hopping fields with FP16 spinors (52 bytes per site and RHS: 12 half2 + one FP32 scale)
+    "f16h-full": 40 * 36, "f16h-2row": 40 * 24, "f16h-8param": 40 * 16,
 }
 # Algorithmic flops per site and right-hand side, the method's count:
 #   80 hops x 4 spins x one 3x3 complex mat-vec (9 complex multiplies x 6 +
@@ -63,7 +65,8 @@ def method_flops(mode):
 
 
 def spinor_bytes(mode):
-    return 2 * (192 if mode.startswith("f64") else 96)  # in + out per site and RHS
+    # in + out per site and RHS
+    return 2 * (192 if mode.startswith("f64") else 52 if mode.startswith("f16h") else 96)
 
 
 def site_bytes(mode, nrhs):
@@ -411,15 +414,20 @@ def native(args, world, rank, local, pg):
         line["cpu_baseline"] = cpu_baseline(mode, seconds=args.cpu_seconds)
     if args.sweep:
         sweep = {}
-        for m in ["f64-full", "f32-full", "f32-2row", "f32-8param", "f16-full", "f16-2row", "f16-8param"]:
+        for m in ["f64-full", "f32-full", "f32-2row", "f32-8param", "f16-full", "f16-2row", "f16-8param",
+                  "f16h-2row"]:
             for nr in ([1] if m.startswith("f64") else [1, 4, 12, 24]):
                 p, c = m.split("-")
                 if p != "f64":
-                    op.store_hops(p, c)
+                    op.store_hops("f16" if p == "f16h" else p, c)
                 sd = torch.complex128 if p == "f64" else torch.complex64
                 xx = synth.gaussian_spinor_torch(L, nr, SEED + 7, device=dev, dtype=sd)
+                if p == "f16h":
+                    xx = op.to_h16(xx)
                 oo = torch.empty_like(xx)
-                if args.threads is not None:
+                if p == "f16h":
+                    pass  # one kernel form, no launch shapes
+                elif args.threads is not None:
                     op.set_threads(p, nr, args.threads)
                 else:
                     op.tune(p, nr)

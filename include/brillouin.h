@@ -30,7 +30,13 @@
  *  - Spinors: device memory, [nrhs][V][4][3] complex (spin, colour) with
  *    interleaved re/im, element type complex128 for BRI_F64 and complex64 for
  *    BRI_F32 and BRI_F16 (BRI_F16 means half-precision hopping fields with
- *    FP32 spinors and FP32 arithmetic).
+ *    FP32 spinors and FP32 arithmetic).  BRI_F16H (apply, overlap kernel and
+ *    bri_convert_spinor only) means half-precision hopping fields with FP16
+ *    spinors: each right-hand side is bri_h16_field_bytes(V) bytes, [V][4][3]
+ *    half2 (re, im) followed by [V] float scales (one per site; entry = half
+ *    value x scale, the scale a power of two with the site's largest
+ *    component in [scale/2, scale)) and unused padding to a multiple of 16
+ *    bytes; arithmetic in FP32.
  *  - Gamma matrices: the hermitian chiral (DeGrand-Rossi) basis,
  *    gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1, 1, -1, -1).
  *  - Ownership: the caller owns every buffer passed in; the library owns the
@@ -66,7 +72,7 @@ typedef enum {
     BRI_ESTATE = -8       /* call out of order (e.g. apply before build_hops) */
 } bri_status;
 
-typedef enum { BRI_F64 = 0, BRI_F32 = 1, BRI_F16 = 2 } bri_prec;
+typedef enum { BRI_F64 = 0, BRI_F32 = 1, BRI_F16 = 2, BRI_F16H = 3 } bri_prec;
 
 /* storage of the hopping fields (each W_d(x) is in SU(3), Sec. 5.2) */
 typedef enum {
@@ -233,6 +239,18 @@ bri_status bri_build_hops_noalloc(const bri_lattice *lat, const double *U, doubl
  * Synchronises the device's default stream.  Errors: BRI_EINVAL, BRI_ECUDA
  * (message via bri_last_error(NULL)). */
 bri_status bri_alu_peak(int prec, double *tflops);
+
+/* Bytes of one right-hand side in the BRI_F16H spinor storage (see the
+ * conventions): 48 V + 4 V rounded up to a multiple of 16.  No device work. */
+size_t bri_h16_field_bytes(int V);
+
+/* Convert nrhs spinor fields between storages: BRI_F64 (complex128), BRI_F32
+ * (complex64) and BRI_F16H (FP16 + per-site scale, rounded to nearest).
+ * dst, src: device buffers of the sizes the storages imply; must not
+ * overlap.  Asynchronous on stream.  Errors: BRI_EINVAL (null or misaligned
+ * pointers, nrhs < 1, another storage, overlap), BRI_ECUDA. */
+bri_status bri_convert_spinor(bri_ctx *ctx, void *dst, bri_prec dst_prec, const void *src, bri_prec src_prec,
+                              int nrhs, void *stream);
 
 /* result[0] + i result[1] = <a, b> = sum conj(a) b over nrhs spinor fields
  * (the dot product of the Krylov solvers, FP64 accumulation: per-block partial

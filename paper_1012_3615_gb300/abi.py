@@ -15,7 +15,7 @@ BRI_OK, BRI_EINVAL, BRI_ENOMEM, BRI_ECUDA, BRI_ENOTCONV, BRI_EBREAKDOWN, BRI_ENA
     0, -1, -2, -3, -4, -5, -6, -7, -8
 STATUS_NAMES = {0: "BRI_OK", -1: "BRI_EINVAL", -2: "BRI_ENOMEM", -3: "BRI_ECUDA", -4: "BRI_ENOTCONV",
                 -5: "BRI_EBREAKDOWN", -6: "BRI_ENAN", -7: "BRI_ETIMEOUT", -8: "BRI_ESTATE"}
-BRI_F64, BRI_F32, BRI_F16 = 0, 1, 2
+BRI_F64, BRI_F32, BRI_F16, BRI_F16H = 0, 1, 2, 3
 BRI_LINK_FULL, BRI_LINK_2ROW, BRI_LINK_8PARAM = 0, 1, 2
 
 
@@ -90,6 +90,8 @@ SIGNATURES = {
     "bri_kernel_launches": (c_long, [c_void_p]),
     "bri_last_error": (ctypes.c_char_p, [c_void_p]),
     "bri_alu_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "bri_h16_field_bytes": (ctypes.c_size_t, [c_int]),
+    "bri_convert_spinor": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_int, c_void_p]),
 }
 
 _lib = None

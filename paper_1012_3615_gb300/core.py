@@ -9,7 +9,7 @@ import torch
 
 from . import abi
 
-_PREC = {"f64": abi.BRI_F64, "f32": abi.BRI_F32, "f16": abi.BRI_F16}
+_PREC = {"f64": abi.BRI_F64, "f32": abi.BRI_F32, "f16": abi.BRI_F16, "f16h": abi.BRI_F16H}
 _COMP = {"full": abi.BRI_LINK_FULL, "2row": abi.BRI_LINK_2ROW, "8param": abi.BRI_LINK_8PARAM}
 
 
@@ -65,7 +65,35 @@ class Brillouin:
         if st != 0:
             raise BriError(st, self.lib.bri_last_error(self.ctx).decode())
 
+    def h16_field_bytes(self):
+        """bytes of one right-hand side in the FP16-spinor storage (prec "f16h")"""
+        return int(self.lib.bri_h16_field_bytes(self.V))
+
+    def to_h16(self, psi):
+        """spinors (complex64 or complex128, (n, V, 4, 3)) to the FP16 storage
+        with per-site scales: a uint8 tensor (n, h16_field_bytes())"""
+        n = self._spinor(psi, "f64" if psi.dtype == torch.complex128 else "f32")
+        out = torch.empty((n, self.h16_field_bytes()), dtype=torch.uint8, device="cuda")
+        self._check(self.lib.bri_convert_spinor(self.ctx, _ptr(out), abi.BRI_F16H, _ptr(psi),
+                                                abi.BRI_F64 if psi.dtype == torch.complex128 else abi.BRI_F32, n,
+                                                _stream()))
+        return out
+
+    def from_h16(self, buf, dtype=torch.complex64):
+        """FP16-storage spinors back to complex64 / complex128 (n, V, 4, 3)"""
+        n = self._spinor(buf, "f16h")
+        out = torch.empty((n, self.V, 4, 3), dtype=dtype, device="cuda")
+        self._check(self.lib.bri_convert_spinor(self.ctx, _ptr(out),
+                                                abi.BRI_F64 if dtype == torch.complex128 else abi.BRI_F32, _ptr(buf),
+                                                abi.BRI_F16H, n, _stream()))
+        return out
+
     def _spinor(self, t, prec):
+        if prec == "f16h":
+            fb = self.h16_field_bytes()
+            if not (t.is_cuda and t.dtype == torch.uint8 and t.is_contiguous() and t.numel() % fb == 0):
+                raise ValueError("FP16 spinors must be a contiguous cuda uint8 tensor of n x %d bytes" % fb)
+            return t.numel() // fb
         dt = spinor_dtype(prec)
         if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise ValueError("spinor must be a contiguous cuda %s tensor" % dt)

@@ -148,13 +148,17 @@ bri_status bri_get_hops(bri_ctx *ctx, double *out, void *stream) {
     return bri_export_hops_impl(ctx, (double2 *)out, as_stream(stream));
 }
 
+static size_t spinor_bytes(bri_ctx *ctx, bri_prec prec, int nrhs) {
+    if (prec == BRI_F16H) return bri_h16_bytes(ctx->g.V) * nrhs;
+    return (prec == BRI_F64 ? 16 : 8) * 12 * (size_t)ctx->g.V * nrhs;
+}
+
 static bri_status check_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, bri_prec prec) {
     if (!out || !in) return bri_fail(ctx, BRI_EINVAL, "null spinor pointer");
     if (!bri_aligned16(out) || !bri_aligned16(in)) return bri_fail(ctx, BRI_EINVAL, "spinors must be 16-byte aligned");
     if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
-    BRI_RETURN_IF(check_prec(ctx, prec));
-    const size_t elt = prec == BRI_F64 ? 16 : 8;
-    const size_t bytes = elt * 12 * (size_t)ctx->g.V * nrhs;
+    if (prec != BRI_F16H) BRI_RETURN_IF(check_prec(ctx, prec));
+    const size_t bytes = spinor_bytes(ctx, prec, nrhs);
     const char *o = (const char *)out, *i = (const char *)in;
     if (o < i + bytes && i < o + bytes) return bri_fail(ctx, BRI_EINVAL, "in and out overlap");
     return BRI_OK;
@@ -164,6 +168,11 @@ bri_status bri_apply(bri_ctx *ctx, void *out, const void *in, int nrhs, double m
                      void *stream) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, prec));
+    if (prec == BRI_F16H) {
+        if (!ctx->f16.valid) return bri_fail(ctx, BRI_ESTATE, "FP16 hopping fields not built");
+        if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "FP16 spinors with the clover term are not built");
+        return bri_dslash_h16(ctx, out, in, nrhs, m0, dagger ? 1 : 0, nullptr, as_stream(stream));
+    }
     return bri_dslash_impl(ctx, out, in, nrhs, m0, dagger ? 1 : 0, prec, as_stream(stream));
 }
 
@@ -186,7 +195,29 @@ bri_status bri_apply_overlap_kernel(bri_ctx *ctx, void *out, const void *in, int
                                     void *stream) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_apply(ctx, out, in, nrhs, prec));
+    if (prec == BRI_F16H) {
+        if (!ctx->f16.valid) return bri_fail(ctx, BRI_ESTATE, "FP16 hopping fields not built");
+        if (ctx->csw != 0.0) return bri_fail(ctx, BRI_ESTATE, "FP16 spinors with the clover term are not built");
+        return bri_dslash_h16(ctx, out, in, nrhs, -rho, 2, nullptr, as_stream(stream));
+    }
     return bri_dslash_impl(ctx, out, in, nrhs, -rho, 2, prec, as_stream(stream));
+}
+
+size_t bri_h16_field_bytes(int V) { return V > 0 ? bri_h16_bytes(V) : 0; }
+
+bri_status bri_convert_spinor(bri_ctx *ctx, void *dst, bri_prec dst_prec, const void *src, bri_prec src_prec,
+                              int nrhs, void *stream) {
+    if (!ctx) return BRI_EINVAL;
+    if (!dst || !src || !bri_aligned16(dst) || !bri_aligned16(src))
+        return bri_fail(ctx, BRI_EINVAL, "dst and src must be 16-byte aligned device pointers");
+    if (nrhs < 1 || nrhs > 65535) return bri_fail(ctx, BRI_EINVAL, "nrhs must be in [1, 65535]");
+    auto fmt = [](bri_prec p) { return p == BRI_F64 ? 0 : p == BRI_F32 ? 1 : p == BRI_F16H ? 3 : -1; };
+    if (fmt(dst_prec) < 0 || fmt(src_prec) < 0)
+        return bri_fail(ctx, BRI_EINVAL, "spinor storages are BRI_F64, BRI_F32 and BRI_F16H");
+    const size_t db = spinor_bytes(ctx, dst_prec, nrhs), sb = spinor_bytes(ctx, src_prec, nrhs);
+    const char *d = (const char *)dst, *c = (const char *)src;
+    if (d < c + sb && c < d + db) return bri_fail(ctx, BRI_EINVAL, "dst and src overlap");
+    return bri_convert_spinor_impl(ctx, dst, fmt(dst_prec), src, fmt(src_prec), nrhs, as_stream(stream));
 }
 
 bri_status bri_solve(bri_ctx *ctx, double *x, const double *b, int nrhs, double m0, double tol, int maxit, int mode,

@@ -92,6 +92,12 @@ bri_status bri_project_impl(bri_ctx *ctx, double2 *Y, const double2 *A, long n, 
 bri_status bri_dslash_impl(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode,
                            bri_prec prec, cudaStream_t s);
 bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s);
+// FP16-spinor apply (BRI_F16H) and spinor storage conversions (dslash_h16.cu)
+size_t bri_h16_bytes(int V);
+bri_status bri_dslash_h16(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, const int *skip,
+                          cudaStream_t s);
+bri_status bri_convert_spinor_impl(bri_ctx *ctx, void *dst, int dfmt, const void *src, int sfmt, int nrhs,
+                                   cudaStream_t s);
 // multi-RHS apply on the tensor cores (launch variant 8; FP32/FP16 full fields)
 // (cap: right-hand sides per warp pass, an even number 2..12; anything else: 12)
 bri_status bri_dslash_tc(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
