@@ -396,6 +396,8 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * adding 10240 the L2 link-prefetch kernel that combines the hops d and -d
  * before their gamma terms, adding 12288 that kernel held to 128 registers,
  * adding 14336 the same pair loop with the gamma terms after the spin loop,
+ * 18432 the loop of 10240 with the per-site part of the link addresses
+ * computed once and the next pair's neighbours carried over,
  * 16384 the tensor-core multi-RHS kernel (Sec. 8 class form as one complex
  * (15 x 240) x (240 x 4 nrhs) product per site on mma.sync with FP16
  * operands and FP32 accumulation; full link storage only, otherwise the
@@ -405,10 +407,10 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * warp takes per pass (an even number 2..12; 0 or anything else: 12).
  * bri_get_threads returns the current choice or a negative bri_status;
  * untuned, 128 threads with: the unrolled kernel (BRI_F64); variant 10240
- * (FP32 full, FP16 2-row fields); 14336 (FP32 2-row, FP16 full fields);
+ * (FP32 full fields); 18432 (FP32 2-row, FP16 full and 2-row fields);
  * 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for
- * nrhs < 1, a negative value, 1..31 or more than 1024 threads, or a variant
- * above 16384. */
+ * nrhs < 1, a negative value, 1..31 or more than 1024 threads (other than
+ * with 16384), or a variant above 18432. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 

@@ -437,7 +437,7 @@ bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_prec(ctx, prec));
     const int thr = threads & 2047, variant = threads >> 11;
-    if (nrhs < 1 || threads < 0 || variant > 8 || (variant < 8 && ((thr > 0 && thr < 32) || thr > 1024)))
+    if (nrhs < 1 || threads < 0 || variant > 9 || (variant != 8 && ((thr > 0 && thr < 32) || thr > 1024)))
         return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
     // variant 8 (tensor cores): the low bits are the right-hand sides per warp pass
     ctx->tune[bri_tune_key(ctx, prec, nrhs)] = variant == 8 ? threads : (thr & ~31) | (variant << 11);
@@ -475,7 +475,7 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     // variants of the FP32 plain kernel (launch shape above bit 11)
     for (int thr : {0, 64, 128, 256, 512, 128 | 2048, 128 | 4096, 256 | 4096, 64 | 6144, 128 | 6144, 128 | 8192,
                     256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288, 128 | 14336,
-                    16384 | 4, 16384 | 6, 16384 | 8, 16384 | 12}) {
+                    16384 | 4, 16384 | 6, 16384 | 8, 16384 | 12, 128 | 18432, 256 | 18432}) {
         if (thr == 0 && (prec == BRI_F64 || !tiled_ok(ctx->g))) continue;
         // the tensor-core kernel has FP16-operand accuracy: a candidate for FP16
         // fields (same accuracy class) with full storage only

@@ -28,18 +28,19 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
 
 // Untuned launch shape per storage format, 128 threads each: FP64 -> unrolled
 // kernel; otherwise the hop-pair loop with L2 link prefetch in the form that
-// was fastest on 32^3x64 for 1-24 right-hand sides: (d, -d) combined before
-// the gamma terms (variant 5) for FP32 full and FP16 2-row fields, with the
-// gamma terms after the spin loop (variant 7) for FP32 2-row and FP16 full
-// fields, variant 5 held to 128 registers (variant 6) for 8-parameter fields.
-// The register allocation, and with it the fastest form, differs between the
-// link decoders.
+// was fastest on 32^3x64 for 1-12 right-hand sides: (d, -d) combined before
+// the gamma terms (variant 5) for FP32 full fields, the same loop with the
+// per-site part of the link addresses computed once and the next pair's
+// neighbours carried over (variant 9) for FP32 2-row, FP16 full and FP16 2-row
+// fields (1-6% faster there, 28% slower for FP32 full), variant 5 held to 128
+// registers (variant 6) for 8-parameter fields.  The register allocation, and
+// with it the fastest form, differs between the link decoders.
 static int default_shape(bri_ctx *ctx, bri_prec prec) {
     if (prec == BRI_F64) return 128;
     const bri_comp c = (prec == BRI_F32 ? ctx->f32 : ctx->f16).comp;
     if (c == BRI_LINK_8PARAM) return 128 | (6 << 11);
-    if (prec == BRI_F32) return c == BRI_LINK_FULL ? 128 | (5 << 11) : 128 | (7 << 11);
-    return c == BRI_LINK_FULL ? 128 | (7 << 11) : 128 | (5 << 11);
+    if (prec == BRI_F32 && c == BRI_LINK_FULL) return 128 | (5 << 11);
+    return 128 | (9 << 11);
 }
 
 // launch shape (threads per block, kernel variant in bits 11+; see

@@ -416,6 +416,47 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
     }
 }
 
+
+// The pair loop of variant 5 with cheaper addressing (launch variant 9): the
+// per-site part of every link address is computed once, each field adds
+// j VP NQ, and the neighbours of the next pair (found for its L2 prefetch)
+// are carried into the next iteration instead of being recomputed.
+template <class LL>
+BRI_D void f32_hops_lean(const LL &ll, const float2 *__restrict__ in, int site, const SiteNb &nb, float rsign,
+                         const Geom &g, AccF &acc) {
+    if (g.nhop == 0) return;
+    const long long sc = ll.cidx(site);
+    int yf, yb;
+    float phf, phb;
+    hop_nb(g.hop[0].dm, site, nb, yf, phf, yb, phb);
+    long long bc = ll.cidx(yb);
+#pragma unroll 1
+    for (int t = 0; t < g.nhop; t++) {
+        const int cyf = yf, cyb = yb;
+        const float cphf = phf, cphb = phb;
+        const long long cbc = bc;
+        if (t + 1 < g.nhop) {
+            const int jn = g.hop[t + 1].j;
+            hop_nb(g.hop[t + 1].dm, site, nb, yf, phf, yb, phb);
+            bc = ll.cidx(yb);
+            ll.prefetch_ci(jn, sc, site);
+            ll.prefetch_ci(jn, bc, yb);
+        }
+        const HopArg hc = g.hop[t];
+        float2 cf[12];
+        {
+            const M3<float2> W = ll.load_ci(hc.j, sc, site);
+            float2 q[12];
+            load_spinor(in + (size_t)cyf * 12, q);
+            colour_mv<1>(W, q, cf);
+        }
+        const M3<float2> W = ll.load_ci(hc.j, cbc, cyb);
+        float2 q[12];
+        load_spinor(in + (size_t)cyb * 12, q);
+        pair_body_s(cf, W, q, hc.lam * cphf, cphf * cphb, hc.rho * rsign * cphf, hc, acc);
+    }
+}
+
 // FP32 stencil loop with the links of pair j + 1 copied asynchronously
 // (cp.async) into this thread's double-buffered shared-memory slots while pair
 // j is computed: the DRAM latency of the links overlaps the arithmetic and
@@ -642,6 +683,8 @@ BRI_D void dslash_body(int mode, const LL &ll, const typename LL::T *__restrict_
             extern __shared__ float4 lslots[];
             const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(lslots) + threadIdx.x * 16u;
             f32_hops_cpasync(ll, in, site, nb, rsign, g, lbase, acc);
+        } else if constexpr (VAR == 9) {
+            f32_hops_lean(ll, in, site, nb, rsign, g, acc);
         } else {
             // VAR 5 (and 6, through k_dslash_r128): pair_body_s; VAR 7: pair_body
             f32_hops<VAR == 1 || VAR >= 5, VAR == 4 ? 1 : VAR == 5 ? 2 : VAR == 7 ? 3 : 0>(ll, in, site, nb, rsign, g,
@@ -860,7 +903,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     const int variant = threads >> 11;
     threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
+    static int max_threads[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
         const int v = (variant == 1 || variant == 2 || variant >= 4) ? variant : 0;
@@ -872,6 +915,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
                           : v == 5 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 5>)
                           : v == 6 ? cudaFuncGetAttributes(&attr, k_dslash_r128<LL>)
                           : v == 7 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 7>)
+                          : v == 9 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 9>)
                                    : cudaFuncGetAttributes(&attr, k_dslash<LL, 0>);
             max_threads[v] = e == cudaSuccess ? attr.maxThreadsPerBlock : 128;
             if (v == 2) {
@@ -888,6 +932,7 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
         else if (v == 5) k_dslash<LL, 5><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 6) k_dslash_r128<LL><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 7) k_dslash<LL, 7><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+        else if (v == 9) k_dslash<LL, 9><<<grid, threads, 0, s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
         else if (v == 2)
             k_dslash<LL, 2><<<grid, threads, threads * 4 * LL::SLOTS * 16, s>>>(mode, ll, (const T *)in, (T *)out, g,
                                                                                  diag, skip);

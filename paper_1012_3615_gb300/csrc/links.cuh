@@ -138,6 +138,33 @@ template <bri_comp C> struct LinkF32 {
         for (int q = 0; q < NQ; q++) prefetch_l2(p + 32 * q);
         if (C == BRI_LINK_FULL) prefetch_l2(b + (size_t)j * VP + site);
     }
+    // chunk offset of site s within any field (field j adds j VP NQ): lets a
+    // loop over fields reuse the per-site part of the address
+    BRI_D long long cidx(int s) const { return (long long)(s & ~31) * NQ + (s & 31); }
+    BRI_D void prefetch_ci(int j, long long ci, int s) const {
+        const float4 *p = a + (long long)j * VP * NQ + ci;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) prefetch_l2(p + 32 * q);
+        if (C == BRI_LINK_FULL) prefetch_l2(b + (long long)j * VP + s);
+    }
+    BRI_D M3<float2> load_ci(int j, long long ci, int s) const {
+        const float4 *p = a + (long long)j * VP * NQ + ci;
+        if (C == BRI_LINK_8PARAM) {
+            float4 v0 = p[0], v1 = p[32];
+            float pr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            return from_eight(pr);
+        }
+        M3<float2> m;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            float4 v = p[32 * q];
+            m.e[2 * q] = make_float2(v.x, v.y);
+            m.e[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        if (C == BRI_LINK_FULL) m.e[8] = b[(long long)j * VP + s];
+        else third_row(m);
+        return m;
+    }
     BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
         M3<float2> m;
         if (C == BRI_LINK_8PARAM) {
@@ -212,6 +239,44 @@ template <bri_comp C> struct LinkF16 {
         } else if (C == BRI_LINK_2ROW) {
             prefetch_l2((const uint2 *)b + (size_t)j * VP + site);
         }
+    }
+    BRI_D long long cidx(int s) const { return NQ == 1 ? (long long)s : (long long)(s & ~31) * NQ + (s & 31); }
+    BRI_D void prefetch_ci(int j, long long ci, int s) const {
+        const uint4 *p = a + (long long)j * VP * NQ + ci;
+        prefetch_l2(p);
+        if (C == BRI_LINK_FULL) {
+            prefetch_l2(p + 32);
+            prefetch_l2((const uint32_t *)b + (long long)j * VP + s);
+        } else if (C == BRI_LINK_2ROW) {
+            prefetch_l2((const uint2 *)b + (long long)j * VP + s);
+        }
+    }
+    BRI_D M3<float2> load_ci(int j, long long ci, int s) const {
+        const uint4 *p = a + (long long)j * VP * NQ + ci;
+        M3<float2> m;
+        if (C == BRI_LINK_FULL) {
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                uint4 v = p[32 * q];
+                m.e[4 * q] = h2f(v.x);
+                m.e[4 * q + 1] = h2f(v.y);
+                m.e[4 * q + 2] = h2f(v.z);
+                m.e[4 * q + 3] = h2f(v.w);
+            }
+            m.e[8] = h2f(((const uint32_t *)b)[(long long)j * VP + s]);
+        } else if (C == BRI_LINK_2ROW) {
+            uint4 v = p[0];
+            uint2 t = ((const uint2 *)b)[(long long)j * VP + s];
+            m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
+            m.e[4] = h2f(t.x); m.e[5] = h2f(t.y);
+            third_row(m);
+        } else {
+            uint4 v = p[0];
+            float2 q0 = h2f(v.x), q1 = h2f(v.y), q2 = h2f(v.z), q3 = h2f(v.w);
+            float pr[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
+            m = from_eight(pr);
+        }
+        return m;
     }
     BRI_D M3<float2> load_smem(uint32_t src, uint32_t stride) const {
         M3<float2> m;

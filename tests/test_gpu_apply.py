@@ -128,7 +128,7 @@ def test_kernel_variants_agree(gpu, prec, comp):
     x = torch.as_tensor(psi, device=gpu)
     outs = []
     for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256, 8192 + 128, 8192 + 256,
-                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128, 7 * 2048 + 128):
+                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128, 7 * 2048 + 128, 9 * 2048 + 128):
         op.set_threads(prec, 2, shape)
         outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
     for shape, o in outs[1:]:
@@ -177,7 +177,7 @@ def test_pair_combined_body_matches_oracle(gpu, prec, comp, L, bc):
                     oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) for r in range(psi.shape[0])]
         finally:
             oracle.reset_weights()
-        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128, 7 * 2048 + 128):
+        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128, 7 * 2048 + 128, 9 * 2048 + 128):
             op.set_threads(prec, 2, shape)
             out = op.apply(x, m0=0.05, prec=prec).cpu().numpy()
             outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
