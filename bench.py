@@ -367,17 +367,21 @@ def native(args, world, rank, local, pg):
     # the stencil slab by slab); every step synchronises
     xh = x.cpu().pin_memory()
     oh = torch.empty_like(xh).pin_memory()
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(10, min(args.steps, 30))
     op.apply_host(xh, 0.0, prec=prec, out=oh)  # staging buffers allocated outside the timing
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    step_s = []
     for _ in range(e2e_steps):
+        t0 = time.perf_counter()
         op.apply_host(xh, 0.0, prec=prec, out=oh)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+        step_s.append(time.perf_counter() - t0)
+    # the median step: a single slow host copy (another tenant on the host) does not set the number
+    e2e_s = sorted(step_s)[len(step_s) // 2]
     e2e = {"value": bytes_step / e2e_s / 1e9 * world, "unit": "GB/s",
            "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
-           "d2h_bytes_per_step": int(oh.numel() * oh.element_size()), "ms_per_step": e2e_s * 1e3}
+           "d2h_bytes_per_step": int(oh.numel() * oh.element_size()), "ms_per_step": e2e_s * 1e3,
+           "ms_per_step_mean": sum(step_s) / len(step_s) * 1e3, "steps": e2e_steps, "statistic": "median step"}
 
     flops = method_flops(mode) * nrhs * V / (ms * 1e-3) / 1e12
     impl_flops = IMPL_FLOPS_PER_SITE * nrhs * V / (ms * 1e-3) / 1e12
