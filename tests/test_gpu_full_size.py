@@ -186,3 +186,33 @@ def test_force_12x12x12x12_finite_differences(gpu):
                 f.append(np.real(np.vdot(chi[sites], oracle.apply_sites(L, AP, Up, 0.0, psi, sites))))
             grad = grad + (1 if part == 0 else 1j) * (f[0] - f[1]) / (2 * eps)
         assert abs(dU[x0, mu, a, bb] - grad) <= 1e-7 * max(abs(grad), 1e-3), (dU[x0, mu, a, bb], grad)
+
+
+def test_tensor_core_and_fp16_spinors_32x32x32x64(gpu):
+    """32^3 x 64 at sampled sites: the tensor-core form with 12 right-hand
+    sides (FP16 full fields, one warp pass) and the FP16-spinor apply (FP16
+    2-row fields), each against the oracle built from the links at the sampled
+    sites (bounds as in the small-lattice tests)."""
+    L = (32, 32, 32, 64)
+    V = synth.volume(L)
+    U = synth.random_su3_links_torch(L, 0.3, 1015, device=gpu)
+    psi = synth.gaussian_spinor_torch(L, 12, 1021, device=gpu).to(torch.complex64)
+    op = Brillouin(L, AP)
+    op.build_hops(U, prec="f16", comp="full")
+    op.set_threads("f16", 12, 16384)
+    out = op.apply(psi, 0.02, prec="f16").cpu().numpy()
+    sites = np.concatenate([[0, V - 1, 31, 32 * 32 * 32 - 1], np.random.default_rng(13).integers(0, V, 4)])
+    Uh = U.cpu().numpy()
+    for r in (0, 5, 11):
+        ref = oracle.apply_sites(L, AP, Uh, 0.02, psi[r].cpu().numpy().astype(np.complex128), sites)
+        err = np.abs(out[r][sites] - ref).max() / np.abs(ref).max()
+        assert err <= 5e-4, (r, err)
+    del out
+    op.store_hops("f16", "2row")
+    xh = op.to_h16(psi[:1].contiguous())
+    dec = op.from_h16(xh, torch.complex128)[0].cpu().numpy()
+    got = op.from_h16(op.apply(xh, 0.02, prec="f16h"), torch.complex128)[0].cpu().numpy()[sites]
+    ref = oracle.apply_sites(L, AP, Uh, 0.02, dec, sites)
+    assert np.abs(got - ref).max() <= 6e-4 * np.abs(ref).max()
+    del op, U, psi
+    torch.cuda.empty_cache()
