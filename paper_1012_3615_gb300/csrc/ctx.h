@@ -102,6 +102,7 @@ bri_status bri_convert_spinor_impl(bri_ctx *ctx, void *dst, int dfmt, const void
 // (cap: right-hand sides per warp pass, an even number 2..12; anything else: 12)
 bri_status bri_dslash_tc(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
                          const int *skip, int cap, cudaStream_t s);
+bri_status bri_tc_reserve(bri_ctx *ctx, int nrhs, int cap);
 // dslash with an explicit launch shape; skip[r] != 0 skips right-hand side r
 bri_status bri_dslash_raw(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
                           const int *skip, int threads, cudaStream_t s);

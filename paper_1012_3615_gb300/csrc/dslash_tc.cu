@@ -352,17 +352,14 @@ static void dslash_tc_launch(int mode, const LL &ll, const void *in, void *out, 
 
 using namespace bri;
 
-// the tensor-core apply for the stored FP32 or FP16 fields of prec (full
-// storage); the caller has checked that they exist
-bri_status bri_dslash_tc(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
-                         const int *skip, int cap, cudaStream_t s) {
-    const Geom &g = ctx->g;
-    const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
-    if (st.comp != BRI_LINK_FULL) return bri_fail(ctx, BRI_EINVAL, "tensor-core apply needs full link storage");
+// work buffers of the tensor-core apply for nrhs right-hand sides (cap: as in
+// bri_dslash_tc); the apply allocates them on first use, which a stream
+// capture does not allow, so callers that capture reserve them first
+bri_status bri_tc_reserve(bri_ctx *ctx, int nrhs, int cap) {
     if (!ctx->tc_amax) BRI_TRY_CUDA(ctx, cudaMalloc(&ctx->tc_amax, sizeof(unsigned) * 65536));
     int rchunk, nt, Rp;
-    tc_chunks(nrhs, cap, rchunk, nt, Rp);
-    const size_t fbytes = (size_t)g.V * Rp * 4 * sizeof(uint4);
+    tc_chunks(nrhs, cap & 511, rchunk, nt, Rp);
+    const size_t fbytes = (size_t)ctx->g.V * Rp * 4 * sizeof(uint4);
     if (ctx->tc_fbytes < fbytes) {
         cudaFree(ctx->tc_f);
         ctx->tc_f = nullptr;
@@ -370,6 +367,17 @@ bri_status bri_dslash_tc(bri_ctx *ctx, void *out, const void *in, int nrhs, doub
         BRI_TRY_CUDA(ctx, cudaMalloc(&ctx->tc_f, fbytes));
         ctx->tc_fbytes = fbytes;
     }
+    return BRI_OK;
+}
+
+// the tensor-core apply for the stored FP32 or FP16 fields of prec (full
+// storage); the caller has checked that they exist
+bri_status bri_dslash_tc(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, bri_prec prec,
+                         const int *skip, int cap, cudaStream_t s) {
+    const Geom &g = ctx->g;
+    const LinkStore &st = prec == BRI_F32 ? ctx->f32 : ctx->f16;
+    if (st.comp != BRI_LINK_FULL) return bri_fail(ctx, BRI_EINVAL, "tensor-core apply needs full link storage");
+    BRI_RETURN_IF(bri_tc_reserve(ctx, nrhs, cap));
     const int VP = (g.V + 31) & ~31;
     const double diag = m0 + g.lamd[0];
     if (prec == BRI_F32)

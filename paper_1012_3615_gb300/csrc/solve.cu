@@ -479,6 +479,13 @@ bri_status bicgstab(bri_ctx *ctx, const VecSet &vs, const T *b, bool have_x0, in
     if (it != w->graphs.end()) {
         exec = it->second;
     } else {
+        // the tensor-core apply and the site-pair kernel allocate on first use:
+        // not inside the capture
+        const int thr = bri_dslash_threads(ctx, prec, nrhs);
+        if ((thr >> 11) == 8) BRI_RETURN_IF(bri_tc_reserve(ctx, nrhs, thr & 2047));
+        if ((thr >> 11) == 3 && prec != BRI_F64 && !(prec == BRI_F32 ? ctx->p32 : ctx->p16).valid &&
+            !ctx->g.clov64)
+            BRI_RETURN_IF(bri_pair_store_impl(ctx, prec, s));
         cudaGraph_t graph;
         BRI_TRY_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         bri_status st = enqueue_iters<T>(ctx, vs, nrhs, m0, prec, K, s);

@@ -74,3 +74,20 @@ def test_noalloc_validates_pointers_without_gpu(lib):
     assert lib.bri_build_hops_noalloc(ctypes.byref(lat), 256, 520, None) == abi.BRI_EINVAL
     assert lib.bri_build_hops_noalloc(ctypes.byref(lat), 264, 512, None) == abi.BRI_EINVAL
     assert b"aligned" in lib.bri_last_error(None)
+
+
+def test_new_entry_points_validate_without_gpu(lib):
+    """The entry points added with the FP16 spinors, the pseudofermion action
+    and the ALU peaks reject bad arguments before any CUDA call."""
+    from paper_1012_3615_gb300 import abi
+
+    # one right-hand side of the FP16-spinor storage: 48 V + 4 V rounded up to 16
+    assert lib.bri_h16_field_bytes(81) == 48 * 81 + 336
+    assert lib.bri_h16_field_bytes(256) == 48 * 256 + 1024
+    assert lib.bri_h16_field_bytes(0) == 0
+    assert lib.bri_convert_spinor(None, 256, abi.BRI_F16H, 512, abi.BRI_F32, 1, None) == abi.BRI_EINVAL
+    assert lib.bri_inverse_action(None, None, None, None, 256, 0.0, 1e-10, 100, None, None) == abi.BRI_EINVAL
+    v = ctypes.c_double()
+    assert lib.bri_alu_peak(7, ctypes.byref(v)) == abi.BRI_EINVAL
+    assert lib.bri_alu_peak(abi.BRI_F32, None) == abi.BRI_EINVAL
+    assert b"prec" in lib.bri_last_error(None)

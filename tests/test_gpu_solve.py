@@ -80,6 +80,27 @@ def test_batched_point_sources_fp32_fields(gpu):
     assert max(i["outer_iters"] for i in info) <= 3
 
 
+@pytest.mark.parametrize("prec,comp,shape,mode", [("f16", "full", 16384, 3), ("f32", "full", 6144 + 64, 4)])
+def test_batched_solve_with_allocating_launch_shapes(gpu, prec, comp, shape, mode):
+    """Launch shapes whose kernels allocate on first use (the tensor-core form,
+    the site-pair kernel) as the inner apply of a batched solve: their buffers
+    are reserved before the iterations are captured as a CUDA graph, and the
+    FP64 defect correction reaches the true residual 1e-10 (the tensor-core
+    apply's FP16-operand error only costs outer cycles)."""
+    L = (4, 4, 4, 4)
+    U = synth.random_su3_links(L, 0.35, 15)
+    b, x0 = synth.point_sources(L, 16)
+    W = oracle.build_hops(L, U)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+    op.set_threads(prec, 12, shape)
+    x, info = op.solve(torch.as_tensor(b, device=gpu), m0=0.0, tol=1e-10, mode=mode)
+    assert all(i["status"] == "BRI_OK" for i in info), info
+    xs = x.cpu().numpy()
+    for r in range(12):
+        assert _true_resid(L, AP, W, 0.0, xs[r], b[r]) <= 1e-10
+
+
 def test_sequential_modes_continue_after_a_failed_rhs(gpu):
     """Modes 1 and 2 take the right-hand sides one after the other; a NaN in the
     first does not stop the second, and the call returns the failing status."""
