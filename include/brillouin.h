@@ -397,7 +397,15 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * before their gamma terms, adding 12288 that kernel held to 128 registers,
  * adding 14336 the same pair loop with the gamma terms after the spin loop,
  * 18432 the loop of 10240 with the per-site part of the link addresses
- * computed once and the next pair's neighbours carried over,
+ * computed once and the next pair's neighbours carried over, 20480 the loop
+ * of 10240 with the links staged in shared memory by 1-D bulk copies
+ * (cp.async.bulk into a ring of stages per warp, completion counted on an
+ * mbarrier; at most 256 threads; with 32 threads and an x extent of 32 one
+ * warp per x line), 22528 the one-warp-per-x-line loop with the neighbour
+ * spinor lines staged by bulk copies as well (x extent 32 only, the low bits
+ * ignored; otherwise as 20480).  A bulk-copy wait that has not completed after
+ * one second gives up, and the next apply call on the context then returns
+ * BRI_ETIMEOUT,
  * 16384 the tensor-core multi-RHS kernel (Sec. 8 class form as one complex
  * (15 x 240) x (240 x 4 nrhs) product per site on mma.sync with FP16
  * operands and FP32 accumulation; full link storage only, otherwise the
@@ -406,16 +414,26 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * class it shares).  For 16384 the low bits give the right-hand sides one
  * warp takes per pass (an even number 2..12; 0 or anything else: 12).
  * bri_get_threads returns the current choice or a negative bri_status;
- * untuned, 128 threads with: the unrolled kernel (BRI_F64); variant 10240
- * (FP32 full fields); 18432 (FP32 2-row, FP16 full and 2-row fields);
- * 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for
- * nrhs < 1, a negative value, 1..31 or more than 1024 threads (other than
- * with 16384), or a variant above 18432. */
+ * untuned: the unrolled kernel at 128 threads (BRI_F64); 128 threads with
+ * variant 10240 (FP32 full fields); 22528 (the other FP32 and FP16 formats on
+ * an x extent of 32); otherwise 128 threads with variant 18432 (FP32 2-row,
+ * FP16 full and 2-row fields) or 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for nrhs < 1, a
+ * negative value, 1..31 or more than 1024 threads (other than with 16384), or
+ * a variant above 22528. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);
 int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs);
 
 /* Number of kernels this context launched so far (diagnostics). */
 long bri_kernel_launches(bri_ctx *ctx);
+
+/* Diagnostics of the bounded waits: with on != 0 the bulk-copy applies (launch
+ * variants 20480 and 22528) announce 16 bytes more to their first link
+ * stage's barrier than its copies deliver, so every warp's wait runs out after
+ * one second, the kernel drains its other copies and returns, and the next
+ * apply call returns BRI_ETIMEOUT (and clears the flag).  No memory is accessed out of bounds
+ * and nothing is left in flight.  on = 0 restores normal operation.
+ * Errors: BRI_EINVAL (null ctx). */
+bri_status bri_debug_stall(bri_ctx *ctx, int on);
 
 /* Description of the last error on ctx (or of the last bri_create failure
  * when ctx is null).  The string stays valid until the next call on ctx. */

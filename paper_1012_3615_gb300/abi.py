@@ -88,6 +88,7 @@ SIGNATURES = {
     "bri_set_threads": (c_int, [c_void_p, c_int, c_int, c_int]),
     "bri_get_threads": (c_int, [c_void_p, c_int, c_int]),
     "bri_kernel_launches": (c_long, [c_void_p]),
+    "bri_debug_stall": (c_int, [c_void_p, c_int]),
     "bri_last_error": (ctypes.c_char_p, [c_void_p]),
     "bri_alu_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
     "bri_h16_field_bytes": (ctypes.c_size_t, [c_int]),

@@ -91,6 +91,13 @@ bri_status bri_create(const bri_lattice *lat, bri_ctx **out) {
         delete ctx;
         return bri_fail(nullptr, BRI_ECUDA, "no CUDA device");
     }
+    if (cudaHostAlloc((void **)&ctx->werr_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&ctx->g.werr, ctx->werr_h, 0) != cudaSuccess) {
+        cudaFreeHost(ctx->werr_h);
+        delete ctx;
+        return bri_fail(nullptr, BRI_ENOMEM, "host-mapped status word");
+    }
+    *ctx->werr_h = 0;
     tune_load(ctx);
     *out = ctx;
     return BRI_OK;
@@ -107,6 +114,7 @@ bri_status bri_destroy(bri_ctx *ctx) {
     cudaFree(ctx->tc_f);
     cudaFree(ctx->U);
     cudaFree(ctx->hops64);
+    cudaFreeHost(ctx->werr_h);
     for (LinkStore *st : {&ctx->f32, &ctx->f16, &ctx->p32, &ctx->p16}) {
         cudaFree(st->a);
         cudaFree(st->b);
@@ -437,7 +445,7 @@ bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_prec(ctx, prec));
     const int thr = threads & 2047, variant = threads >> 11;
-    if (nrhs < 1 || threads < 0 || variant > 9 || (variant != 8 && ((thr > 0 && thr < 32) || thr > 1024)))
+    if (nrhs < 1 || threads < 0 || variant > 11 || (variant != 8 && ((thr > 0 && thr < 32) || thr > 1024)))
         return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
     // variant 8 (tensor cores): the low bits are the right-hand sides per warp pass
     ctx->tune[bri_tune_key(ctx, prec, nrhs)] = variant == 8 ? threads : (thr & ~31) | (variant << 11);
@@ -448,6 +456,12 @@ int bri_get_threads(bri_ctx *ctx, bri_prec prec, int nrhs) {
     if (!ctx) return BRI_EINVAL;
     if (check_prec(ctx, prec) != BRI_OK || nrhs < 1) return BRI_EINVAL;
     return bri_dslash_threads(ctx, prec, nrhs);
+}
+
+bri_status bri_debug_stall(bri_ctx *ctx, int on) {
+    if (!ctx) return BRI_EINVAL;
+    ctx->g.stall = on ? 1 : 0;
+    return BRI_OK;
 }
 
 long bri_kernel_launches(bri_ctx *ctx) { return ctx ? ctx->launches : 0; }
@@ -475,7 +489,8 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     // variants of the FP32 plain kernel (launch shape above bit 11)
     for (int thr : {0, 64, 128, 256, 512, 128 | 2048, 128 | 4096, 256 | 4096, 64 | 6144, 128 | 6144, 128 | 8192,
                     256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288, 128 | 14336,
-                    16384 | 4, 16384 | 6, 16384 | 8, 16384 | 12, 128 | 18432, 256 | 18432}) {
+                    16384 | 4, 16384 | 6, 16384 | 8, 16384 | 12, 128 | 18432, 256 | 18432, 32 | 20480,
+                    128 | 20480, 32 | 22528}) {
         if (thr == 0 && (prec == BRI_F64 || !tiled_ok(ctx->g))) continue;
         // the tensor-core kernel has FP16-operand accuracy: a candidate for FP16
         // fields (same accuracy class) with full storage only

@@ -151,11 +151,16 @@ constexpr int TX = 8, TY = 4, TZ = 2, TT = 2;
 // class weights of |d|_1 and the offset of d within the shared-memory halo tile.
 struct HopArg {
     int dm[4];
-    int j;
+    // j and ge as 16-bit values keep the struct at 48 bytes, a multiple of 16:
+    // the kernels index g.hop[] by a run-time hop number, and at 52 bytes the
+    // FP32 stencil loop took two more registers and ran 17% slower
+    short j;
+    short ge;  // first hop index after this hop's run of equal (d_y, d_z, d_t)
     int hd;
     float lam, rho;
     float fd[4];  // d_mu as floats (no conversions in the hop loop)
 };
+static_assert(sizeof(HopArg) == 48, "HopArg: keep a multiple of 16 bytes");
 
 // Lattice geometry and the class weights of the operator (lambda_0..4,
 // rho_0..4 with rho_0 unused; by default the der_iso / lap_bri weights above).
@@ -180,6 +185,11 @@ struct Geom {
     // sites an apply covers, [s0, s1) (the whole lattice: 0, V); a t-slab of
     // the lattice is a contiguous range
     int s0, s1;
+    // set to 1 by a kernel whose bounded wait gave up (host-mapped, read by
+    // the next apply call); stall != 0 makes the bulk-copy kernel announce 16
+    // bytes more than its first stage delivers, so that its waits run out
+    int *werr;
+    int stall;
 };
 inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) {
     for (int n = 0; n < 5; n++) {
@@ -197,10 +207,18 @@ inline void geom_set_weights(Geom &g, const double lam[5], const double rho[5]) 
             h.dm[mu] = off_comp(k, mu);
             h.fd[mu] = (float)h.dm[mu];
         }
-        h.j = j;
+        h.j = (short)j;
         h.hd = h.dm[0] + (TX + 2) * (h.dm[1] + (TY + 2) * (h.dm[2] + (TZ + 2) * h.dm[3]));
         h.lam = g.lam[n];
         h.rho = g.rho[n];
+    }
+    // the hops of one run of equal (d_y, d_z, d_t) (d_x = -1, 0, 1: consecutive
+    // canonical indices) read their neighbour spinors from the same two x lines
+    for (int t = g.nhop - 1; t >= 0; t--) {
+        const HopArg &h = g.hop[t];
+        const bool same = t + 1 < g.nhop && g.hop[t + 1].dm[1] == h.dm[1] && g.hop[t + 1].dm[2] == h.dm[2] &&
+                          g.hop[t + 1].dm[3] == h.dm[3];
+        g.hop[t].ge = (short)(same ? g.hop[t + 1].ge : t + 1);
     }
 }
 

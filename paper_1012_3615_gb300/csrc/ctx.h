@@ -37,6 +37,7 @@ struct bri_ctx {
     unsigned *tc_amax = nullptr;   // per-RHS max |psi| of the tensor-core apply (65536 entries)
     void *tc_f = nullptr;          // FP16 copy of the spinors for the tensor-core apply
     size_t tc_fbytes = 0;
+    int *werr_h = nullptr;         // host-mapped wait-timeout flag (g.werr is its device address)
     long gen = 0;  // bumped whenever the operator changes (links, weights)
     std::map<std::string, int> tune;  // launch-shape cache: key -> threads per block
     std::string err;

@@ -26,20 +26,24 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
     return buf;
 }
 
-// Untuned launch shape per storage format, 128 threads each: FP64 -> unrolled
-// kernel; otherwise the hop-pair loop with L2 link prefetch in the form that
-// was fastest on 32^3x64 for 1-12 right-hand sides: (d, -d) combined before
-// the gamma terms (variant 5) for FP32 full fields, the same loop with the
-// per-site part of the link addresses computed once and the next pair's
-// neighbours carried over (variant 9) for FP32 2-row, FP16 full and FP16 2-row
-// fields (1-6% faster there, 28% slower for FP32 full), variant 5 held to 128
-// registers (variant 6) for 8-parameter fields.  The register allocation, and
-// with it the fastest form, differs between the link decoders.
+// Untuned launch shape per storage format: FP64 -> unrolled kernel (128
+// threads).  FP32 full fields: the hop-pair loop with L2 link prefetch, (d, -d)
+// combined before the gamma terms (variant 5, 128 threads).  The other FP32 and
+// FP16 formats on an x extent of 32: the line kernel with the links and
+// neighbour spinors staged by bulk copies (variant 11, one warp per x line),
+// 1-10% faster there on 32^3x64 (1% slower than variant 5 for FP32 full
+// fields, whose 21.6 KB of stages per warp hold it to 10 warps per SM).  Other
+// extents, 128 threads: the variant-5 loop with the per-site part of the link
+// addresses computed once and the next pair's neighbours carried over
+// (variant 9) for FP32 2-row, FP16 full and FP16 2-row fields, variant 5 held
+// to 128 registers (variant 6) for 8-parameter fields.  The register
+// allocation, and with it the fastest form, differs between the link decoders.
 static int default_shape(bri_ctx *ctx, bri_prec prec) {
     if (prec == BRI_F64) return 128;
     const bri_comp c = (prec == BRI_F32 ? ctx->f32 : ctx->f16).comp;
-    if (c == BRI_LINK_8PARAM) return 128 | (6 << 11);
     if (prec == BRI_F32 && c == BRI_LINK_FULL) return 128 | (5 << 11);
+    if (ctx->g.L[0] == 32) return 32 | (11 << 11);
+    if (c == BRI_LINK_8PARAM) return 128 | (6 << 11);
     return 128 | (9 << 11);
 }
 
@@ -73,6 +77,10 @@ bri_status bri_dslash_range(bri_ctx *ctx, void *out, const void *in, int nrhs, d
 
 static bri_status dslash_geom(bri_ctx *ctx, const Geom &g, void *out, const void *in, int nrhs, double m0, int mode,
                               bri_prec prec, const int *skip, int threads, cudaStream_t s) {
+    if (ctx->werr_h && *(volatile int *)ctx->werr_h) {
+        *(volatile int *)ctx->werr_h = 0;
+        return bri_fail(ctx, BRI_ETIMEOUT, "a bounded wait of an earlier apply gave up; its output is invalid");
+    }
     const double diag = m0 + g.lamd[0];
     if (prec == BRI_F64) {
         if (!ctx->have64) return bri_fail(ctx, BRI_ESTATE, "FP64 hopping fields not built");

@@ -506,6 +506,98 @@ BRI_D void f32_hops_cpasync(const LL &ll, const float2 *__restrict__ in, int sit
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// ---- bulk-copy link pipeline (launch variant 10) ---------------------------
+// Every warp stages the links of its coming pairs in a ring of ST shared-memory
+// stages.  A stage holds 32-site blocks ("runs", LL::RUN_A + LL::RUN_B bytes)
+// of the pair's field j: the block of the warp's own 32 sites (forward hop,
+// W_d(x)) and the blocks that hold lane 0's and lane 31's x - d (reversed hop,
+// W_d(x - d)).  NB = 1 stages lane 0's block only, which holds every lane's
+// x - d when the x extent is 32 (a warp is one x line, and x - d is one x line
+// again).  Lane 0 issues the runs as 1-D bulk copies, counted in bytes on the
+// stage's mbarrier, ST - 1 pairs ahead of the pair being computed, so the
+// links cost each lane neither address arithmetic nor prefetch instructions; a
+// lane whose x - d lies in no staged block loads that link from global memory.
+// A wait that has not completed after BULK_WAIT_NS gives up: the loop drains
+// the stages still in flight (with the same limit) and returns false.
+constexpr unsigned long long BULK_WAIT_NS = 1000000000ull;
+
+template <class LL, int NB>
+BRI_D void bulk_issue(const LL &ll, const Geom &g, int t, int site, const SiteNb &nb, int wblk, uint32_t dst,
+                      uint32_t bar, uint32_t extra) {
+    constexpr uint32_t RUN = LL::RUN_A + LL::RUN_B;
+    int yf, yb;
+    float pf, pb;
+    hop_nb(g.hop[t].dm, site, nb, yf, pf, yb, pb);
+    const int c0 = __shfl_sync(0xffffffffu, yb >> 5, 0);
+    const int c1 = NB == 2 ? __shfl_sync(0xffffffffu, yb >> 5, 31) : c0;
+    if ((threadIdx.x & 31) == 0) {
+        const int j = g.hop[t].j;
+        fence_async_smem();
+        mbar_arrive_tx(bar, (c1 != c0 ? 3u : 2u) * RUN + extra);
+        ll.bulk_run(j, wblk, dst, bar);
+        ll.bulk_run(j, c0, dst + RUN, bar);
+        if (c1 != c0) ll.bulk_run(j, c1, dst + 2 * RUN, bar);
+    }
+}
+
+template <class LL, int ST, int NB>
+BRI_D bool f32_hops_bulk(const LL &ll, const float2 *__restrict__ in, int site, int wblk, const SiteNb &nb,
+                         float rsign, const Geom &g, uint32_t ring, uint32_t bars, AccF &acc) {
+    constexpr uint32_t RUN = LL::RUN_A + LL::RUN_B;
+    constexpr uint32_t STAGE = RUN * (1 + NB);
+    const int lane = (int)threadIdx.x & 31;
+    const int nh = g.nhop;
+    const uint32_t extra0 = g.stall ? 16u : 0u;
+#pragma unroll
+    for (int t = 0; t < ST - 1; t++)
+        if (t < nh) bulk_issue<LL, NB>(ll, g, t, site, nb, wblk, ring + STAGE * t, bars + 8u * t, t == 0 ? extra0 : 0u);
+    int s = 0;          // stage of pair t
+    uint32_t par = 0;   // parity of its current phase
+#pragma unroll 1
+    for (int t = 0; t < nh; t++) {
+        if (t + ST - 1 < nh) {
+            // the stage pair t - 1 used: every lane has read it
+            __syncwarp();
+            const int sn = s == 0 ? ST - 1 : s - 1;
+            bulk_issue<LL, NB>(ll, g, t + ST - 1, site, nb, wblk, ring + STAGE * sn, bars + 8u * sn, 0u);
+        }
+        const HopArg hc = g.hop[t];
+        int yf, yb;
+        float phf, phb;
+        hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+        const int c0 = __shfl_sync(0xffffffffu, yb >> 5, 0);
+        const int c1 = NB == 2 ? __shfl_sync(0xffffffffu, yb >> 5, 31) : c0;
+        const uint32_t cur = ring + STAGE * s;
+        if (!mbar_wait(bars + 8u * s, par, BULK_WAIT_NS)) {
+            // drain the later stages this warp has issued, then give up
+            int sd = s;
+            uint32_t pd = par;
+            for (int u = t + 1; u < nh && u < t + ST; u++) {
+                if (++sd == ST) { sd = 0; pd ^= 1u; }
+                mbar_wait(bars + 8u * sd, pd, BULK_WAIT_NS);
+            }
+            return false;
+        }
+        float2 cf[12];
+        {
+            const M3<float2> W = ll.load_run(cur, lane);
+            float2 q[12];
+            load_spinor(in + (size_t)yf * 12, q);
+            colour_mv<1>(W, q, cf);
+        }
+        const int cb = yb >> 5;
+        M3<float2> W;
+        if (cb == c0) W = ll.load_run(cur + RUN, yb & 31);
+        else if (NB == 2 && cb == c1) W = ll.load_run(cur + 2 * RUN, yb & 31);
+        else W = ll.load(hc.j, yb);
+        float2 q[12];
+        load_spinor(in + (size_t)yb * 12, q);
+        pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+        if (++s == ST) { s = 0; par ^= 1u; }
+    }
+    return true;
+}
+
 // FP64 row products chi[c] = sum_c' w_cc' p_c' of spin sp as explicit FMA
 // chains (one multiply and five FMAs per real component): w = W (SGN = 1) or
 // W^dagger (SGN = -1).  Complex products followed by complex adds would cost
@@ -649,13 +741,40 @@ BRI_D void clover_add(const Geom &g, int site, const T p[12], T o[12]) {
     }
 }
 
+// out(x) = diag psi(x) + the hop sum (+ the clover term), times gamma_5 for mode 2
+template <typename T, bool CLOV>
+BRI_D void dslash_finish(int mode, const T *__restrict__ in, T *__restrict__ out, int site, const Geom &g, double diag,
+                         const typename AccOf<T>::A &acc) {
+    using R = typename RealOf<T>::R;
+    T p[12];
+    load_spinor(in + (size_t)site * 12, p);
+    const R dg = (R)diag;
+    T o[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        T v;
+        v.x = dg * p[i].x + acc.a[i].x;
+        v.y = dg * p[i].y + acc.a[i].y;
+        if constexpr (sizeof(T) == 8) {
+            v.x -= acc.ai[i].y;
+            v.y += acc.ai[i].x;
+        }
+        o[i] = v;
+    }
+    if constexpr (CLOV) clover_add(g, site, p, o);
+    if (mode == 2) {
+#pragma unroll
+        for (int i = 6; i < 12; i++) { o[i].x = -o[i].x; o[i].y = -o[i].y; }
+    }
+    store_spinor(out + (size_t)site * 12, o);
+}
+
 // CLOV: add the clover term of Geom in the epilogue (a separate instantiation,
 // so that the kernels without it keep their register budget)
 template <class LL, int VAR, bool CLOV>
 BRI_D void dslash_body(int mode, const LL &ll, const typename LL::T *__restrict__ in, typename LL::T *__restrict__ out,
                        const Geom &g, double diag, const int *__restrict__ skip) {
     using T = typename LL::T;
-    using R = typename RealOf<T>::R;
     // grid.x = site blocks x right-hand sides with the RHS fastest, so the blocks
     // of all RHS over the same sites run together and read each link from DRAM
     // once (the others hit L2)
@@ -693,27 +812,7 @@ BRI_D void dslash_body(int mode, const LL &ll, const typename LL::T *__restrict_
     } else {
         all_hops(std::make_integer_sequence<int, NCANON>{}, ll, in, site, nb, rsign, g, acc);
     }
-    T p[12];
-    load_spinor(in + (size_t)site * 12, p);
-    const R dg = (R)diag;
-    T o[12];
-#pragma unroll
-    for (int i = 0; i < 12; i++) {
-        T v;
-        v.x = dg * p[i].x + acc.a[i].x;
-        v.y = dg * p[i].y + acc.a[i].y;
-        if constexpr (sizeof(T) == 8) {
-            v.x -= acc.ai[i].y;
-            v.y += acc.ai[i].x;
-        }
-        o[i] = v;
-    }
-    if constexpr (CLOV) clover_add(g, site, p, o);
-    if (mode == 2) {
-#pragma unroll
-        for (int i = 6; i < 12; i++) { o[i].x = -o[i].x; o[i].y = -o[i].y; }
-    }
-    store_spinor(out + (size_t)site * 12, o);
+    dslash_finish<T, CLOV>(mode, in, out, site, g, diag, acc);
 }
 
 template <class LL, int VAR, bool CLOV = false>
@@ -727,6 +826,330 @@ __global__ void __maxnreg__(128) k_dslash_r128(int mode, LL ll, const typename L
                                                typename LL::T *__restrict__ out, Geom g, double diag,
                                                const int *__restrict__ skip) {
     dslash_body<LL, 5, false>(mode, ll, in, out, g, diag, skip);
+}
+
+// launch variant 10: the bulk-copy link pipeline.  Needs s0 a multiple of 32
+// (every warp covers one 32-site block); lanes past s1 compute on the range's
+// last site and store nothing.  Dynamic shared memory: bulk_smem<LL, ST, NB>.
+template <class LL, int ST, int NB> BRI_HD constexpr uint32_t bulk_bar_bytes(int warps) {
+    return (uint32_t)((8 * ST * warps + 127) & ~127);
+}
+template <class LL, int ST, int NB> BRI_HD constexpr uint32_t bulk_smem(int warps) {
+    return bulk_bar_bytes<LL, ST, NB>(warps) + (uint32_t)warps * ST * (1 + NB) * (LL::RUN_A + LL::RUN_B);
+}
+template <class LL, int ST, int NB>
+__global__ void k_dslash_bulk(int mode, LL ll, const float2 *__restrict__ in, float2 *__restrict__ out, Geom g,
+                              double diag, const int *__restrict__ skip) {
+    extern __shared__ __align__(128) unsigned char bulk_sm[];
+    const int nblk = (g.s1 - g.s0 + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int nr = (int)gridDim.x / nblk;
+    const int rhs = (int)blockIdx.x % nr;
+    const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5;
+    const int wsite = g.s0 + ((int)blockIdx.x / nr) * (int)blockDim.x + warp * 32;  // lane 0's site
+    if (wsite >= g.s1) return;  // the whole warp is past the range
+    if (skip && skip[rhs]) return;
+    const bool active = wsite + lane < g.s1;
+    const int site = active ? wsite + lane : g.s1 - 1;
+    const size_t off = (size_t)rhs * g.V * 12;
+    in += off;
+    out += off;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(bulk_sm);
+    const uint32_t bars = base + 8u * ST * warp;
+    const uint32_t ring = base + bulk_bar_bytes<LL, ST, NB>((int)blockDim.x >> 5) +
+                          (uint32_t)warp * ST * (1 + NB) * (LL::RUN_A + LL::RUN_B);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < ST; i++) mbar_init(bars + 8u * i, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    int x[4];
+    const SiteNb nb = site_nb(g, site, x);
+    AccF acc;
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc.a[i] = acc.ai[i] = make_float2(0.f, 0.f);
+    const float rsign = mode == 1 ? -1.f : 1.f;
+    if (!f32_hops_bulk<LL, ST, NB>(ll, in, site, wsite >> 5, nb, rsign, g, ring, bars, acc)) {
+        if (lane == 0 && g.werr) *(volatile int *)g.werr = 1;
+        return;
+    }
+    if (active) dslash_finish<float2, false>(mode, in, out, site, g, diag, acc);
+}
+
+// Launch variant 10 at 32 threads per block with an x extent of 32: one warp
+// per block and one x line per warp.  The operands of every copy (the block's
+// line, the line holding x - d, the field) then follow from blockIdx and the
+// pair index alone, the same in every lane, and every lane's x - d lies in the
+// one staged backward run: no shuffles, no fallback loads.  Needs s0 and s1
+// multiples of 32.  Dynamic shared memory: 128 + ST x 2 runs.
+template <class LL, int ST>
+__global__ void __launch_bounds__(32) k_dslash_bulk_line(int mode, LL ll, const float2 *__restrict__ in,
+                                                         float2 *__restrict__ out, Geom g, double diag,
+                                                         const int *__restrict__ skip) {
+    extern __shared__ __align__(128) unsigned char bulk_sm[];
+    constexpr uint32_t RUN = LL::RUN_A + LL::RUN_B;
+    constexpr uint32_t STAGE = 2 * RUN;
+    const int nl = (g.s1 - g.s0) >> 5;
+    const int nr = (int)gridDim.x / nl;
+    const int rhs = (int)blockIdx.x % nr;
+    const int line = (g.s0 >> 5) + (int)blockIdx.x / nr;
+    if (skip && skip[rhs]) return;
+    const int lane = (int)threadIdx.x;
+    const int site = line * 32 + lane;
+    const size_t off = (size_t)rhs * g.V * 12;
+    in += off;
+    out += off;
+    const uint32_t bars = (uint32_t)__cvta_generic_to_shared(bulk_sm);
+    const uint32_t ring = bars + 128u;
+    const int L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+    const int ly = line % L1, lz = (line / L1) % L2, lt = line / (L1 * L2);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < ST; i++) mbar_init(bars + 8u * i, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    int x[4];
+    const SiteNb nb = site_nb(g, site, x);
+    AccF acc;
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc.a[i] = acc.ai[i] = make_float2(0.f, 0.f);
+    const float rsign = mode == 1 ? -1.f : 1.f;
+    const int nh = g.nhop;
+    // the runs of pair t into stage sn: field j at this line and at the line of x - d
+    auto issue = [&](int t, int sn, uint32_t extra) {
+        const HopArg &h = g.hop[t];
+        int y = ly - h.dm[1], z = lz - h.dm[2], w = lt - h.dm[3];
+        y += y < 0 ? L1 : y >= L1 ? -L1 : 0;
+        z += z < 0 ? L2 : z >= L2 ? -L2 : 0;
+        w += w < 0 ? L3 : w >= L3 ? -L3 : 0;
+        const int bl = y + L1 * (z + L2 * w);
+        if (lane == 0) {
+            const uint32_t bar = bars + 8u * sn, dst = ring + STAGE * sn;
+            mbar_arrive_tx(bar, 2 * RUN + extra);
+            ll.bulk_run(h.j, line, dst, bar);
+            ll.bulk_run(h.j, bl, dst + RUN, bar);
+        }
+    };
+#pragma unroll
+    for (int t = 0; t < ST - 1; t++)
+        if (t < nh) issue(t, t, t == 0 && g.stall ? 16u : 0u);
+    int s = 0;
+    uint32_t par = 0;
+    bool ok = true;
+#pragma unroll 1
+    for (int t = 0; t < nh; t++) {
+        if (t + ST - 1 < nh) {
+            __syncwarp();  // every lane has read the stage pair t - 1 used
+            issue(t + ST - 1, s == 0 ? ST - 1 : s - 1, 0u);
+        }
+        const HopArg hc = g.hop[t];
+        int yf, yb;
+        float phf, phb;
+        hop_nb(hc.dm, site, nb, yf, phf, yb, phb);
+        const uint32_t cur = ring + STAGE * s;
+        if (!mbar_wait(bars + 8u * s, par, BULK_WAIT_NS)) {
+            int sd = s;
+            uint32_t pd = par;
+            for (int u = t + 1; u < nh && u < t + ST; u++) {
+                if (++sd == ST) { sd = 0; pd ^= 1u; }
+                mbar_wait(bars + 8u * sd, pd, BULK_WAIT_NS);
+            }
+            ok = false;
+            break;
+        }
+        float2 cf[12];
+        {
+            const M3<float2> W = ll.load_run(cur, lane);
+            float2 q[12];
+            load_spinor(in + (size_t)yf * 12, q);
+            colour_mv<1>(W, q, cf);
+        }
+        const M3<float2> W = ll.load_run(cur + RUN, yb & 31);
+        float2 q[12];
+        load_spinor(in + (size_t)yb * 12, q);
+        pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+        if (++s == ST) { s = 0; par ^= 1u; }
+    }
+    if (!ok) {
+        if (lane == 0 && g.werr) *(volatile int *)g.werr = 1;
+        return;
+    }
+    dslash_finish<float2, false>(mode, in, out, site, g, diag, acc);
+}
+
+// Launch variant 11: the line kernel with the neighbour spinors staged too.
+// The hops of one group, the (up to three) pairs that differ only in d_x, read
+// their spinors from the same two x lines, the line shifted by
+// +(d_y, d_z, d_t) and the one shifted by -(d_y, d_z, d_t); a ring of two
+// spinor stages holds both lines (3,072 bytes each) of the current group while
+// the next group's are copied, beside a ring of two link stages.  A lane then
+// finds psi(x + d) at slot (x + d_x) mod 32 of the forward line and
+// psi(x - d) at slot (x - d_x) mod 32 of the backward one, and its boundary
+// phase is the group's (uniform) y, z, t part times its own x part; the lines
+// and phases are worked out once per group.  The loop has no global loads and
+// no per-lane neighbour arithmetic left.  Needs an x extent of 32 and s0, s1
+// multiples of 32.  Dynamic shared memory: line2_smem<LL>().
+template <class LL> BRI_HD constexpr unsigned line2_smem() { return 128u + 4u * (LL::RUN_A + LL::RUN_B) + 4u * 3072u; }
+
+struct LineShift {
+    int fl, bl;    // the lines shifted by +(d_y, d_z, d_t) and by -(d_y, d_z, d_t)
+    float uf, ub;  // boundary phases of their y, z, t wraps
+};
+
+template <class LL>
+__global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const float2 *__restrict__ in,
+                                                          float2 *__restrict__ out, Geom g, double diag,
+                                                          const int *__restrict__ skip) {
+    extern __shared__ __align__(128) unsigned char bulk_sm[];
+    constexpr uint32_t RUN = LL::RUN_A + LL::RUN_B;
+    constexpr uint32_t LSTAGE = 2 * RUN;
+    constexpr uint32_t SLINE = 32u * 12u * 8u;  // one x line of FP32 spinors
+    constexpr uint32_t SSTAGE = 2 * SLINE;
+    const int nl = (g.s1 - g.s0) >> 5;
+    const int nr = (int)gridDim.x / nl;
+    const int rhs = (int)blockIdx.x % nr;
+    const int line = (g.s0 >> 5) + (int)blockIdx.x / nr;
+    if (skip && skip[rhs]) return;
+    const int lane = (int)threadIdx.x;
+    const int site = line * 32 + lane;
+    const size_t off = (size_t)rhs * g.V * 12;
+    in += off;
+    out += off;
+    // barriers: link stages 0, 1, spinor stages 0, 1
+    const uint32_t lbars = (uint32_t)__cvta_generic_to_shared(bulk_sm);
+    const uint32_t sbars = lbars + 16u;
+    const uint32_t lring = lbars + 128u;
+    const uint32_t sring = lring + 2 * LSTAGE;
+    const int L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+    const int ly = line % L1, lz = (line / L1) % L2, lt = line / (L1 * L2);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) mbar_init(lbars + 8u * i, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    AccF acc;
+#pragma unroll
+    for (int i = 0; i < 12; i++) acc.a[i] = acc.ai[i] = make_float2(0.f, 0.f);
+    const float rsign = mode == 1 ? -1.f : 1.f;
+    const float e31 = lane == 31 ? (float)g.bc[0] : 1.f, e0 = lane == 0 ? (float)g.bc[0] : 1.f;
+    const int nh = g.nhop;
+    auto wrap = [](int c, int n, float &ph, float b) {
+        if (c < 0) { ph *= b; return c + n; }
+        if (c >= n) { ph *= b; return c - n; }
+        return c;
+    };
+    auto shifts = [&](int t) {
+        const HopArg &h = g.hop[t];
+        LineShift r;
+        r.uf = r.ub = 1.f;
+        const float b1 = (float)g.bc[1], b2 = (float)g.bc[2], b3 = (float)g.bc[3];
+        r.fl = wrap(ly + h.dm[1], L1, r.uf, b1) +
+               L1 * (wrap(lz + h.dm[2], L2, r.uf, b2) + L2 * wrap(lt + h.dm[3], L3, r.uf, b3));
+        r.bl = wrap(ly - h.dm[1], L1, r.ub, b1) +
+               L1 * (wrap(lz - h.dm[2], L2, r.ub, b2) + L2 * wrap(lt - h.dm[3], L3, r.ub, b3));
+        return r;
+    };
+    auto issue_links = [&](int t, int bl, int sn, uint32_t extra) {
+        if (lane == 0) {
+            const uint32_t bar = lbars + 8u * sn, dst = lring + LSTAGE * sn;
+            mbar_arrive_tx(bar, 2 * RUN + extra);
+            ll.bulk_run(g.hop[t].j, line, dst, bar);
+            ll.bulk_run(g.hop[t].j, bl, dst + RUN, bar);
+        }
+    };
+    auto issue_spinors = [&](const LineShift &ls, int sn) {
+        if (lane == 0) {
+            const uint32_t bar = sbars + 8u * sn, dst = sring + SSTAGE * sn;
+            mbar_arrive_tx(bar, 2 * SLINE);
+            bulk_g2s(dst, in + (size_t)ls.fl * 384, SLINE, bar);
+            bulk_g2s(dst + SLINE, in + (size_t)ls.bl * 384, SLINE, bar);
+        }
+    };
+    if (nh > 0) {
+        LineShift cur = shifts(0), nxt = cur;
+        int gend = g.hop[0].ge;  // first pair of the next group
+        issue_spinors(cur, 0);
+        if (gend < nh) {
+            nxt = shifts(gend);
+            issue_spinors(nxt, 1);
+        }
+        issue_links(0, cur.bl, 0, g.stall ? 16u : 0u);
+        int gi = 0;  // group of pair t
+        int t = 0;
+        bool ok = true;
+        // pair t in link stage S (= t mod 2)
+        auto step = [&](int t, auto S) -> bool {
+            constexpr int s = decltype(S)::value;
+            if (t == gend) {
+                gi++;
+                cur = nxt;
+                gend = g.hop[t].ge;
+                if (gend < nh) {
+                    nxt = shifts(gend);
+                    __syncwarp();  // the stage of group gi + 1 is the one group gi - 1 used
+                    issue_spinors(nxt, (gi + 1) & 1);
+                }
+            }
+            if (t + 1 < nh) {
+                __syncwarp();  // every lane has read the link stage pair t - 1 used
+                issue_links(t + 1, t + 1 < gend ? cur.bl : nxt.bl, s ^ 1, 0u);
+            }
+            if (!mbar_wait(lbars + 8u * s, (uint32_t)(t >> 1) & 1u, BULK_WAIT_NS)) return false;
+            // (waiting on the spinor stage at every pair, not just the group's
+            // first, measured faster: the conditional form takes 13 more registers)
+            if (!mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS))
+                return false;
+            const HopArg hc = g.hop[t];
+            const int dx = hc.dm[0];
+            const float phf = cur.uf * (dx > 0 ? e31 : dx < 0 ? e0 : 1.f);
+            const float phb = cur.ub * (dx > 0 ? e0 : dx < 0 ? e31 : 1.f);
+            const uint32_t lk = lring + LSTAGE * (uint32_t)s;
+            const uint32_t sp = sring + SSTAGE * (uint32_t)(gi & 1);
+            const uint32_t sf = (uint32_t)((lane + dx) & 31), sb = (uint32_t)((lane - dx) & 31);
+            float2 cf[12];
+            {
+                const M3<float2> W = ll.load_run(lk, lane);
+                float2 q[12];
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const float4 v = lds4(sp + 96u * sf + 16u * k);
+                    q[2 * k] = make_float2(v.x, v.y);
+                    q[2 * k + 1] = make_float2(v.z, v.w);
+                }
+                colour_mv<1>(W, q, cf);
+            }
+            const M3<float2> W = ll.load_run(lk + RUN, (int)sb);
+            float2 q[12];
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                const float4 v = lds4(sp + SLINE + 96u * sb + 16u * k);
+                q[2 * k] = make_float2(v.x, v.y);
+                q[2 * k + 1] = make_float2(v.z, v.w);
+            }
+            pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+            return true;
+        };
+        // two pairs per trip, so that the link stage of each is a constant
+#pragma unroll 1
+        for (; t < nh; t += 2) {
+            if (!step(t, std::integral_constant<int, 0>{})) { ok = false; break; }
+            if (t + 1 < nh && !step(t + 1, std::integral_constant<int, 1>{})) { ok = false; t++; break; }
+        }
+        if (!ok) {
+            // wait (bounded) for the stages still in flight: the links of pairs
+            // t and t + 1 and the spinors of groups gi and gi + 1
+            for (int u = t; u < nh && u < t + 2; u++)
+                mbar_wait(lbars + 8u * (uint32_t)(u & 1), (uint32_t)(u >> 1) & 1u, BULK_WAIT_NS);
+            mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS);
+            if (gend < nh)
+                mbar_wait(sbars + 8u * (uint32_t)((gi + 1) & 1), (uint32_t)((gi + 1) >> 1) & 1u, BULK_WAIT_NS);
+            if (lane == 0 && g.werr) *(volatile int *)g.werr = 1;
+            return;
+        }
+    }
+    dslash_finish<float2, false>(mode, in, out, site, g, diag, acc);
 }
 
 // ---- shared-memory tiled variant (FP32 spinors) ------------------------------
@@ -903,10 +1326,67 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     const int variant = threads >> 11;
     threads &= 2047;
     if (threads == 0) threads = 128;
-    static int max_threads[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
+    static int max_threads[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // per-kernel limit from its register use
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
-        const int v = (variant == 1 || variant == 2 || variant >= 4) ? variant : 0;
+        if (variant == 11 && g.L[0] == 32 && g.s0 % 32 == 0 && g.s1 % 32 == 0) {
+            // line kernel with staged links and spinors, one warp per block
+            static bool l2_attr = false;
+            if (!l2_attr) {
+                cudaFuncSetAttribute(k_dslash_bulk_line2<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)line2_smem<LL>());
+                l2_attr = true;
+            }
+            grid = dim3((unsigned)((g.s1 - g.s0) / 32) * (unsigned)nrhs);
+            k_dslash_bulk_line2<LL><<<grid, 32, line2_smem<LL>(), s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+            return;
+        }
+        if (variant >= 10 && g.s0 % 32 == 0) {
+            // bulk-copy link pipeline: 3 stages of 2 runs when a warp is one x
+            // line (x extent 32), else 2 stages of 3 runs
+            const bool line = g.L[0] == 32;
+            static bool attr_set = false;
+            if (max_threads[10] == 0) {
+                cudaFuncAttributes a1, a2;
+                const bool ok = cudaFuncGetAttributes(&a1, k_dslash_bulk<LL, 3, 1>) == cudaSuccess &&
+                                cudaFuncGetAttributes(&a2, k_dslash_bulk<LL, 2, 2>) == cudaSuccess;
+                max_threads[10] = ok ? (a1.maxThreadsPerBlock < a2.maxThreadsPerBlock ? a1.maxThreadsPerBlock
+                                                                                      : a2.maxThreadsPerBlock)
+                                     : 128;
+                if (max_threads[10] > 256) max_threads[10] = 256;
+            }
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_dslash_bulk<LL, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bulk_smem<LL, 3, 1>(8));
+                cudaFuncSetAttribute(k_dslash_bulk<LL, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bulk_smem<LL, 2, 2>(8));
+                attr_set = true;
+            }
+            if (line && threads == 32 && g.s1 % 32 == 0) {
+                // one warp per block, one x line per warp
+                static bool line_attr = false;
+                if (!line_attr) {
+                    cudaFuncSetAttribute(k_dslash_bulk_line<LL, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         128 + 3 * 2 * (int)(LL::RUN_A + LL::RUN_B));
+                    line_attr = true;
+                }
+                grid = dim3((unsigned)((g.s1 - g.s0) / 32) * (unsigned)nrhs);
+                k_dslash_bulk_line<LL, 3><<<grid, 32, 128 + 3 * 2 * (LL::RUN_A + LL::RUN_B), s>>>(
+                    mode, ll, (const T *)in, (T *)out, g, diag, skip);
+                return;
+            }
+            if (threads > max_threads[10]) threads = max_threads[10] & ~31;
+            grid = dim3((unsigned)((g.s1 - g.s0 + threads - 1) / threads) * (unsigned)nrhs);
+            const int w = threads >> 5;
+            if (line)
+                k_dslash_bulk<LL, 3, 1><<<grid, threads, bulk_smem<LL, 3, 1>(w), s>>>(mode, ll, (const T *)in, (T *)out,
+                                                                                     g, diag, skip);
+            else
+                k_dslash_bulk<LL, 2, 2><<<grid, threads, bulk_smem<LL, 2, 2>(w), s>>>(mode, ll, (const T *)in, (T *)out,
+                                                                                     g, diag, skip);
+            return;
+        }
+        const int v = (variant == 1 || variant == 2 || (variant >= 4 && variant <= 9)) ? variant : variant >= 10 ? 5 : 0;
         if (max_threads[v] == 0) {
             cudaFuncAttributes attr;
             cudaError_t e = v == 1 ? cudaFuncGetAttributes(&attr, k_dslash<LL, 1>)

@@ -96,6 +96,67 @@ BRI_D uint4 lds4u(uint32_t a) {
     return v;
 }
 
+BRI_D float2 lds2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+BRI_D uint2 lds2u(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+BRI_D uint32_t lds1u(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// ---- 1-D bulk copies into shared memory, completion counted on an mbarrier ----
+// (cp.async.bulk: source and destination 16-byte aligned, size a multiple of
+// 16 bytes; the mbarrier's phase completes when its expected arrivals have
+// arrived and the announced bytes have landed)
+BRI_D void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// makes the initialised barriers visible to the copy engine
+BRI_D void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival that also announces the bytes the stage's copies deliver
+BRI_D void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+BRI_D bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+BRI_D unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the phase of the given parity; false if it has not completed after
+// limit_ns nanoseconds (the caller reports BRI_ETIMEOUT)
+BRI_D bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+// orders this thread's earlier shared-memory accesses (and those of the lanes
+// it synchronised with) before its later bulk copies into the same bytes
+BRI_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+BRI_D void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // L2 prefetch of one 16-byte chunk (brings the line to L2, no register cost)
 BRI_D void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
@@ -162,6 +223,34 @@ template <bri_comp C> struct LinkF32 {
             m.e[2 * q + 1] = make_float2(v.z, v.w);
         }
         if (C == BRI_LINK_FULL) m.e[8] = b[(long long)j * VP + s];
+        else third_row(m);
+        return m;
+    }
+    // One 32-site block of field j as the bulk-copy kernel stages it: the NQ
+    // chunk rows (RUN_A bytes; chunk q of slot l at 512 q + 16 l), then for
+    // full storage the block's 32 third-row entries (8 bytes each).  Both parts
+    // are contiguous in global memory and start on 256-byte boundaries.
+    static constexpr uint32_t RUN_A = 512u * NQ;
+    static constexpr uint32_t RUN_B = C == BRI_LINK_FULL ? 256u : 0u;
+    BRI_D void bulk_run(int j, int blk, uint32_t dst, uint32_t bar) const {
+        bulk_g2s(dst, a + ((size_t)j * VP + 32 * (size_t)blk) * NQ, RUN_A, bar);
+        if (RUN_B) bulk_g2s(dst + RUN_A, b + (size_t)j * VP + 32 * (size_t)blk, RUN_B, bar);
+    }
+    BRI_D M3<float2> load_run(uint32_t run, int l) const {
+        const uint32_t p = run + 16u * (uint32_t)l;
+        if (C == BRI_LINK_8PARAM) {
+            float4 v0 = lds4(p), v1 = lds4(p + 512);
+            float pr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            return from_eight(pr);
+        }
+        M3<float2> m;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            float4 v = lds4(p + 512 * q);
+            m.e[2 * q] = make_float2(v.x, v.y);
+            m.e[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        if (C == BRI_LINK_FULL) m.e[8] = lds2(run + RUN_A + 8u * (uint32_t)l);
         else third_row(m);
         return m;
     }
@@ -272,6 +361,38 @@ template <bri_comp C> struct LinkF16 {
             third_row(m);
         } else {
             uint4 v = p[0];
+            float2 q0 = h2f(v.x), q1 = h2f(v.y), q2 = h2f(v.z), q3 = h2f(v.w);
+            float pr[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
+            m = from_eight(pr);
+        }
+        return m;
+    }
+    // one 32-site block of field j as the bulk-copy kernel stages it (see
+    // LinkF32): NQ chunk rows of 512 bytes, then the tail entries (4 bytes per
+    // site for full, 8 for 2-row storage)
+    static constexpr uint32_t RUN_A = 512u * NQ;
+    static constexpr uint32_t RUN_B = C == BRI_LINK_FULL ? 128u : C == BRI_LINK_2ROW ? 256u : 0u;
+    BRI_D void bulk_run(int j, int blk, uint32_t dst, uint32_t bar) const {
+        bulk_g2s(dst, a + ((size_t)j * VP + 32 * (size_t)blk) * NQ, RUN_A, bar);
+        if (C == BRI_LINK_FULL) bulk_g2s(dst + RUN_A, (const uint32_t *)b + (size_t)j * VP + 32 * (size_t)blk, RUN_B, bar);
+        if (C == BRI_LINK_2ROW) bulk_g2s(dst + RUN_A, (const uint2 *)b + (size_t)j * VP + 32 * (size_t)blk, RUN_B, bar);
+    }
+    BRI_D M3<float2> load_run(uint32_t run, int l) const {
+        const uint32_t p = run + 16u * (uint32_t)l;
+        M3<float2> m;
+        if (C == BRI_LINK_FULL) {
+            uint4 v = lds4u(p), w = lds4u(p + 512);
+            m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
+            m.e[4] = h2f(w.x); m.e[5] = h2f(w.y); m.e[6] = h2f(w.z); m.e[7] = h2f(w.w);
+            m.e[8] = h2f(lds1u(run + RUN_A + 4u * (uint32_t)l));
+        } else if (C == BRI_LINK_2ROW) {
+            uint4 v = lds4u(p);
+            uint2 t = lds2u(run + RUN_A + 8u * (uint32_t)l);
+            m.e[0] = h2f(v.x); m.e[1] = h2f(v.y); m.e[2] = h2f(v.z); m.e[3] = h2f(v.w);
+            m.e[4] = h2f(t.x); m.e[5] = h2f(t.y);
+            third_row(m);
+        } else {
+            uint4 v = lds4u(p);
             float2 q0 = h2f(v.x), q1 = h2f(v.y), q2 = h2f(v.z), q3 = h2f(v.w);
             float pr[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
             m = from_eight(pr);

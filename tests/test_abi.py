@@ -91,3 +91,4 @@ def test_new_entry_points_validate_without_gpu(lib):
     assert lib.bri_alu_peak(7, ctypes.byref(v)) == abi.BRI_EINVAL
     assert lib.bri_alu_peak(abi.BRI_F32, None) == abi.BRI_EINVAL
     assert b"prec" in lib.bri_last_error(None)
+    assert lib.bri_debug_stall(None, 1) == abi.BRI_EINVAL

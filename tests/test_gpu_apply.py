@@ -119,7 +119,8 @@ def test_tiled_kernel_equals_plain_kernel(gpu, prec, comp):
 def test_kernel_variants_agree(gpu, prec, comp):
     """Every launch shape of the FP32-arithmetic stencil (plain kernel at several
     block sizes, register link prefetch, cp.async link prefetch, fewer-register
-    form, (d, -d) pair-combined form) computes the same result to FP32 rounding."""
+    form, (d, -d) pair-combined form, bulk-copy link pipeline) computes the
+    same result to FP32 rounding."""
     L, bc = (6, 5, 4, 8), AP
     U = synth.random_su3_links(L, 0.4, 41)
     psi = synth.gaussian_spinor(L, 2, 42).astype(np.complex64)
@@ -128,7 +129,8 @@ def test_kernel_variants_agree(gpu, prec, comp):
     x = torch.as_tensor(psi, device=gpu)
     outs = []
     for shape in (128, 64, 256, 2048 + 128, 4096 + 64, 4096 + 128, 4096 + 256, 8192 + 128, 8192 + 256,
-                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128, 7 * 2048 + 128, 9 * 2048 + 128):
+                  5 * 2048 + 64, 5 * 2048 + 128, 5 * 2048 + 256, 6 * 2048 + 128, 7 * 2048 + 128, 9 * 2048 + 128,
+                  10 * 2048 + 64, 10 * 2048 + 128, 10 * 2048 + 256, 11 * 2048 + 32):
         op.set_threads(prec, 2, shape)
         outs.append((shape, op.apply(x, -0.2, dagger=True, prec=prec)))
     for shape, o in outs[1:]:
@@ -161,8 +163,8 @@ def test_pair_kernel_matches_oracle(gpu, prec, comp, L, bc):
 @pytest.mark.parametrize("L,bc", [((3, 5, 4, 6), AP), ((4, 4, 4, 4), PER)])
 def test_pair_combined_body_matches_oracle(gpu, prec, comp, L, bc):
     """The loops that combine the hops d and -d before the gamma terms (launch
-    variants 5-7) against the oracle for D, D^dagger and the overlap kernel, with
-    the Brillouin and the Wilson weights."""
+    variants 5-7, 9, 10) against the oracle for D, D^dagger and the overlap
+    kernel, with the Brillouin and the Wilson weights."""
     tol = TOL_MAX[(prec, comp)]
     U, psi, W = _setup(L, bc, 60 + sum(L))
     for name in ("brillouin", "wilson"):
@@ -177,7 +179,8 @@ def test_pair_combined_body_matches_oracle(gpu, prec, comp, L, bc):
                     oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) for r in range(psi.shape[0])]
         finally:
             oracle.reset_weights()
-        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128, 7 * 2048 + 128, 9 * 2048 + 128):
+        for shape in (5 * 2048 + 64, 5 * 2048 + 128, 6 * 2048 + 128, 7 * 2048 + 128, 9 * 2048 + 128,
+                      10 * 2048 + 128):
             op.set_threads(prec, 2, shape)
             out = op.apply(x, m0=0.05, prec=prec).cpu().numpy()
             outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
@@ -186,6 +189,38 @@ def test_pair_combined_body_matches_oracle(gpu, prec, comp, L, bc):
                 _check(out[r], ref[r][0], tol, (shape, name, "D"))
                 _check(outd[r], ref[r][1], tol, (shape, name, "Ddag"))
                 _check(outh[r], ref[r][2], tol, (shape, name, "H"))
+
+
+@pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f32", "2row"), ("f32", "8param"), ("f16", "full"),
+                                       ("f16", "2row"), ("f16", "8param")])
+@pytest.mark.parametrize("L,bc", [((32, 3, 4, 4), AP), ((16, 4, 3, 4), PER), ((64, 3, 3, 3), AP),
+                                  ((3, 5, 4, 6), AP)])
+def test_bulk_copy_kernel_matches_oracle(gpu, prec, comp, L, bc):
+    """The bulk-copy link pipeline (launch variant 10) against the oracle for
+    D, D^dagger and the overlap kernel, at 32, 64 and 128 threads.  The x
+    extents cover its cases: 32 (a warp is one x line, every x - d in one
+    staged block, three stages; at 32 threads the one-warp-per-block line
+    kernel), 16 and 64 (x - d in two blocks, two stages of three runs), 3 (a
+    warp spans many x lines: lanes outside the staged blocks load their
+    reversed links from global memory; 360 sites, a ragged last warp).
+    Variant 11 (x extent 32: links and neighbour spinor lines staged, two or
+    three link stages) falls back to variant 10 at the other extents."""
+    tol = TOL_MAX[(prec, comp)]
+    U, psi, W = _setup(L, bc, 70 + sum(L))
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+    x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
+    ref = [(oracle.apply(L, bc, W, -0.1, psi[r]), oracle.apply(L, bc, W, -0.1, psi[r], dagger=True),
+            oracle.overlap_kernel(L, bc, W, 0.0, 1.0, psi[r])) for r in range(psi.shape[0])]
+    for shape in (10 * 2048 + 32, 10 * 2048 + 64, 10 * 2048 + 128, 11 * 2048 + 32, 11 * 2048 + 64):
+        op.set_threads(prec, 2, shape)
+        out = op.apply(x, m0=-0.1, prec=prec).cpu().numpy()
+        outd = op.apply(x, m0=-0.1, dagger=True, prec=prec).cpu().numpy()
+        outh = op.overlap_kernel(x, rho=1.0, prec=prec).cpu().numpy()
+        for r in range(psi.shape[0]):
+            _check(out[r], ref[r][0], tol, (shape, "D"))
+            _check(outd[r], ref[r][1], tol, (shape, "Ddag"))
+            _check(outh[r], ref[r][2], tol, (shape, "H"))
 
 
 def test_multi_rhs_equals_single(gpu):

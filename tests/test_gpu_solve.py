@@ -139,3 +139,23 @@ def test_nan_and_zero_sources(gpu):
         x, info = op.solve(z, m0=0.0, mode=mode)
         assert info[0]["status"] == "BRI_OK"
         assert torch.count_nonzero(x) == 0
+
+
+@pytest.mark.parametrize("mode,prec", [(1, "f32"), (2, "f16"), (4, "f32")])
+def test_solves_on_the_bulk_copy_line_kernel(gpu, mode, prec):
+    """x extent 32: the inner applies use the default line kernel with bulk-copy
+    staging (launch variant 11), whose first launch happens while the solver
+    captures its iterations as a CUDA graph.  The true residual still reaches
+    1e-10."""
+    L = (32, 3, 3, 4)
+    U = synth.random_su3_links(L, 0.35, 21)
+    b = synth.z2_spinor(L, 2 if mode == 4 else 1, 22)
+    W = oracle.build_hops(L, U)
+    op = Brillouin(L, AP)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp="2row")
+    assert op.threads(prec, b.shape[0]) >> 11 == 11
+    x, info = op.solve(torch.as_tensor(b, device=gpu), m0=-0.05, tol=1e-10, mode=mode)
+    assert all(i["status"] == "BRI_OK" for i in info), info
+    xs = x.cpu().numpy()
+    for r in range(b.shape[0]):
+        assert _true_resid(L, AP, W, -0.05, xs[r], b[r]) <= 1e-10
