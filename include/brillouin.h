@@ -402,8 +402,9 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * (cp.async.bulk into a ring of stages per warp, completion counted on an
  * mbarrier; at most 256 threads; with 32 threads and an x extent of 32 one
  * warp per x line), 22528 the one-warp-per-x-line loop with the neighbour
- * spinor lines staged by bulk copies as well (x extent 32 only, the low bits
- * ignored; otherwise as 20480).  A bulk-copy wait that has not completed after
+ * spinor lines staged by bulk copies as well (x extent 32 only, otherwise as
+ * 20480; one warp per block whatever the low bits, which select one buffer per
+ * spinor line when 64 and a two-deep ring of them otherwise).  A bulk-copy wait that has not completed after
  * one second gives up, and the next apply call on the context then returns
  * BRI_ETIMEOUT,
  * 16384 the tensor-core multi-RHS kernel (Sec. 8 class form as one complex
@@ -414,10 +415,10 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * class it shares).  For 16384 the low bits give the right-hand sides one
  * warp takes per pass (an even number 2..12; 0 or anything else: 12).
  * bri_get_threads returns the current choice or a negative bri_status;
- * untuned: the unrolled kernel at 128 threads (BRI_F64); 128 threads with
- * variant 10240 (FP32 full fields); 22528 (the other FP32 and FP16 formats on
- * an x extent of 32); otherwise 128 threads with variant 18432 (FP32 2-row,
- * FP16 full and 2-row fields) or 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for nrhs < 1, a
+ * untuned: the unrolled kernel at 128 threads (BRI_F64); on an x extent of
+ * 32, 22528 + 64 (FP32 full fields) or 22528 + 32 (the other FP32 and FP16
+ * formats); otherwise 128 threads with variant 10240 (FP32 full fields), 18432
+ * (FP32 2-row, FP16 full and 2-row fields) or 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for nrhs < 1, a
  * negative value, 1..31 or more than 1024 threads (other than with 16384), or
  * a variant above 22528. */
 bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads);

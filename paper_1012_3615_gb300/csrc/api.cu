@@ -490,7 +490,7 @@ bri_status bri_tune_impl(bri_ctx *ctx, bri_prec prec, int nrhs, cudaStream_t s) 
     for (int thr : {0, 64, 128, 256, 512, 128 | 2048, 128 | 4096, 256 | 4096, 64 | 6144, 128 | 6144, 128 | 8192,
                     256 | 8192, 512 | 8192, 64 | 10240, 128 | 10240, 256 | 10240, 128 | 12288, 128 | 14336,
                     16384 | 4, 16384 | 6, 16384 | 8, 16384 | 12, 128 | 18432, 256 | 18432, 32 | 20480,
-                    128 | 20480, 32 | 22528}) {
+                    128 | 20480, 32 | 22528, 64 | 22528}) {
         if (thr == 0 && (prec == BRI_F64 || !tiled_ok(ctx->g))) continue;
         // the tensor-core kernel has FP16-operand accuracy: a candidate for FP16
         // fields (same accuracy class) with full storage only

@@ -989,15 +989,23 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line(int mode, LL ll, const 
 // phase is the group's (uniform) y, z, t part times its own x part; the lines
 // and phases are worked out once per group.  The loop has no global loads and
 // no per-lane neighbour arithmetic left.  Needs an x extent of 32 and s0, s1
-// multiples of 32.  Dynamic shared memory: line2_smem<LL>().
-template <class LL> BRI_HD constexpr unsigned line2_smem() { return 128u + 4u * (LL::RUN_A + LL::RUN_B) + 4u * 3072u; }
+// multiples of 32.  Dynamic shared memory: line2_smem<LL, SB>().
+//
+// SB = true keeps one buffer per spinor line instead of a two-deep ring: the
+// forward line of the next group is copied as soon as the group's last pair
+// has consumed its forward spinors, the backward line once it has consumed
+// the backward ones.  That gives up about half a pair of lead for 6 KB less
+// shared memory per warp (13 instead of 10 warps per SM for FP32 full fields).
+template <class LL, bool SB> BRI_HD constexpr unsigned line2_smem() {
+    return 128u + 4u * (LL::RUN_A + LL::RUN_B) + (SB ? 2u : 4u) * 3072u;
+}
 
 struct LineShift {
     int fl, bl;    // the lines shifted by +(d_y, d_z, d_t) and by -(d_y, d_z, d_t)
     float uf, ub;  // boundary phases of their y, z, t wraps
 };
 
-template <class LL>
+template <class LL, bool SB>
 __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const float2 *__restrict__ in,
                                                           float2 *__restrict__ out, Geom g, double diag,
                                                           const int *__restrict__ skip) {
@@ -1016,7 +1024,7 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
     const size_t off = (size_t)rhs * g.V * 12;
     in += off;
     out += off;
-    // barriers: link stages 0, 1, spinor stages 0, 1
+    // barriers: link stages 0, 1, spinor stages 0, 1 (SB: forward line, backward line)
     const uint32_t lbars = (uint32_t)__cvta_generic_to_shared(bulk_sm);
     const uint32_t sbars = lbars + 16u;
     const uint32_t lring = lbars + 128u;
@@ -1067,13 +1075,27 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
             bulk_g2s(dst + SLINE, in + (size_t)ls.bl * 384, SLINE, bar);
         }
     };
+    // SB: one line into buffer k (0 forward, 1 backward)
+    auto issue_line = [&](int ln, int k) {
+        if (lane == 0) {
+            const uint32_t bar = sbars + 8u * k;
+            mbar_arrive_tx(bar, SLINE);
+            bulk_g2s(sring + SLINE * k, in + (size_t)ln * 384, SLINE, bar);
+        }
+    };
     if (nh > 0) {
         LineShift cur = shifts(0), nxt = cur;
         int gend = g.hop[0].ge;  // first pair of the next group
-        issue_spinors(cur, 0);
-        if (gend < nh) {
-            nxt = shifts(gend);
-            issue_spinors(nxt, 1);
+        if constexpr (SB) {
+            issue_line(cur.fl, 0);
+            issue_line(cur.bl, 1);
+            if (gend < nh) nxt = shifts(gend);
+        } else {
+            issue_spinors(cur, 0);
+            if (gend < nh) {
+                nxt = shifts(gend);
+                issue_spinors(nxt, 1);
+            }
         }
         issue_links(0, cur.bl, 0, g.stall ? 16u : 0u);
         int gi = 0;  // group of pair t
@@ -1088,8 +1110,10 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
                 gend = g.hop[t].ge;
                 if (gend < nh) {
                     nxt = shifts(gend);
-                    __syncwarp();  // the stage of group gi + 1 is the one group gi - 1 used
-                    issue_spinors(nxt, (gi + 1) & 1);
+                    if constexpr (!SB) {
+                        __syncwarp();  // the stage of group gi + 1 is the one group gi - 1 used
+                        issue_spinors(nxt, (gi + 1) & 1);
+                    }
                 }
             }
             if (t + 1 < nh) {
@@ -1099,15 +1123,23 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
             if (!mbar_wait(lbars + 8u * s, (uint32_t)(t >> 1) & 1u, BULK_WAIT_NS)) return false;
             // (waiting on the spinor stage at every pair, not just the group's
             // first, measured faster: the conditional form takes 13 more registers)
-            if (!mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS))
-                return false;
+            uint32_t sp;  // the group's forward line; its backward line follows at + SLINE
+            if constexpr (SB) {
+                if (!mbar_wait(sbars, (uint32_t)gi & 1u, BULK_WAIT_NS)) return false;
+                sp = sring;
+            } else {
+                if (!mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS))
+                    return false;
+                sp = sring + SSTAGE * (uint32_t)(gi & 1);
+            }
             const HopArg hc = g.hop[t];
             const int dx = hc.dm[0];
             const float phf = cur.uf * (dx > 0 ? e31 : dx < 0 ? e0 : 1.f);
             const float phb = cur.ub * (dx > 0 ? e0 : dx < 0 ? e31 : 1.f);
             const uint32_t lk = lring + LSTAGE * (uint32_t)s;
-            const uint32_t sp = sring + SSTAGE * (uint32_t)(gi & 1);
             const uint32_t sf = (uint32_t)((lane + dx) & 31), sb = (uint32_t)((lane - dx) & 31);
+            // SB: the group's last pair releases each line buffer to the next group
+            const bool last = SB && t + 1 == gend && gend < nh;
             float2 cf[12];
             {
                 const M3<float2> W = ll.load_run(lk, lane);
@@ -1120,6 +1152,13 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
                 }
                 colour_mv<1>(W, q, cf);
             }
+            if (last) {
+                __syncwarp();  // every lane has consumed its forward spinor
+                issue_line(nxt.fl, 0);
+            }
+            if constexpr (SB) {
+                if (!mbar_wait(sbars + 8u, (uint32_t)gi & 1u, BULK_WAIT_NS)) return false;
+            }
             const M3<float2> W = ll.load_run(lk + RUN, (int)sb);
             float2 q[12];
 #pragma unroll
@@ -1129,6 +1168,10 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
                 q[2 * k + 1] = make_float2(v.z, v.w);
             }
             pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+            if (last) {
+                __syncwarp();  // every lane has consumed its backward spinor
+                issue_line(nxt.bl, 1);
+            }
             return true;
         };
         // two pairs per trip, so that the link stage of each is a constant
@@ -1142,9 +1185,18 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
             // t and t + 1 and the spinors of groups gi and gi + 1
             for (int u = t; u < nh && u < t + 2; u++)
                 mbar_wait(lbars + 8u * (uint32_t)(u & 1), (uint32_t)(u >> 1) & 1u, BULK_WAIT_NS);
-            mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS);
-            if (gend < nh)
-                mbar_wait(sbars + 8u * (uint32_t)((gi + 1) & 1), (uint32_t)((gi + 1) >> 1) & 1u, BULK_WAIT_NS);
+            if constexpr (SB) {
+                // group gi's lines, then group gi + 1's if they were issued (if not,
+                // the wait on that unarmed phase runs out after its limit)
+                for (uint32_t k = 0; k < 2; k++) {
+                    mbar_wait(sbars + 8u * k, (uint32_t)gi & 1u, BULK_WAIT_NS);
+                    if (gend < nh) mbar_wait(sbars + 8u * k, (uint32_t)(gi + 1) & 1u, BULK_WAIT_NS);
+                }
+            } else {
+                mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS);
+                if (gend < nh)
+                    mbar_wait(sbars + 8u * (uint32_t)((gi + 1) & 1), (uint32_t)((gi + 1) >> 1) & 1u, BULK_WAIT_NS);
+            }
             if (lane == 0 && g.werr) *(volatile int *)g.werr = 1;
             return;
         }
@@ -1333,12 +1385,19 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
             // line kernel with staged links and spinors, one warp per block
             static bool l2_attr = false;
             if (!l2_attr) {
-                cudaFuncSetAttribute(k_dslash_bulk_line2<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)line2_smem<LL>());
+                cudaFuncSetAttribute(k_dslash_bulk_line2<LL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)line2_smem<LL, false>());
+                cudaFuncSetAttribute(k_dslash_bulk_line2<LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)line2_smem<LL, true>());
                 l2_attr = true;
             }
             grid = dim3((unsigned)((g.s1 - g.s0) / 32) * (unsigned)nrhs);
-            k_dslash_bulk_line2<LL><<<grid, 32, line2_smem<LL>(), s>>>(mode, ll, (const T *)in, (T *)out, g, diag, skip);
+            if (threads == 64)
+                k_dslash_bulk_line2<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(mode, ll, (const T *)in,
+                                                                                       (T *)out, g, diag, skip);
+            else
+                k_dslash_bulk_line2<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(mode, ll, (const T *)in,
+                                                                                         (T *)out, g, diag, skip);
             return;
         }
         if (variant >= 10 && g.s0 % 32 == 0) {
