@@ -1059,29 +1059,19 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
                L1 * (wrap(lz - h.dm[2], L2, r.ub, b2) + L2 * wrap(lt - h.dm[3], L3, r.ub, b3));
         return r;
     };
+    // the copies are issued by one elected lane of the converged warp
+    // (the copies are issued by one elected lane of the converged warp)
     auto issue_links = [&](int t, int bl, int sn, uint32_t extra) {
-        if (lane == 0) {
-            const uint32_t bar = lbars + 8u * sn, dst = lring + LSTAGE * sn;
-            mbar_arrive_tx(bar, 2 * RUN + extra);
-            ll.bulk_run(g.hop[t].j, line, dst, bar);
-            ll.bulk_run(g.hop[t].j, bl, dst + RUN, bar);
-        }
+        ll.bulk_pair(g.hop[t].j, line, bl, lring + LSTAGE * sn, lbars + 8u * sn, extra);
     };
     auto issue_spinors = [&](const LineShift &ls, int sn) {
-        if (lane == 0) {
-            const uint32_t bar = sbars + 8u * sn, dst = sring + SSTAGE * sn;
-            mbar_arrive_tx(bar, 2 * SLINE);
-            bulk_g2s(dst, in + (size_t)ls.fl * 384, SLINE, bar);
-            bulk_g2s(dst + SLINE, in + (size_t)ls.bl * 384, SLINE, bar);
-        }
+        const uint32_t dst = sring + SSTAGE * sn;
+        bulk_elect2(sbars + 8u * sn, 2 * SLINE, dst, in + (size_t)ls.fl * 384, SLINE, dst + SLINE,
+                    in + (size_t)ls.bl * 384, SLINE);
     };
     // SB: one line into buffer k (0 forward, 1 backward)
     auto issue_line = [&](int ln, int k) {
-        if (lane == 0) {
-            const uint32_t bar = sbars + 8u * k;
-            mbar_arrive_tx(bar, SLINE);
-            bulk_g2s(sring + SLINE * k, in + (size_t)ln * 384, SLINE, bar);
-        }
+        bulk_elect1(sbars + 8u * k, SLINE, sring + SLINE * k, in + (size_t)ln * 384, SLINE);
     };
     if (nh > 0) {
         LineShift cur = shifts(0), nxt = cur;
