@@ -310,6 +310,21 @@ def time_apply(op, x, out, mode, nrhs, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps  # ms per apply
 
 
+def rel_err_vs_fp64(op, x, y, prec):
+    """max |y - y64| / max |y64|, y64 the library's FP64 apply of the same input
+    (m0 = 0; the tests hold the FP64 apply to 1e-13 of the oracle): the
+    per-element error of a reduced-precision storage mode at full size."""
+    import torch
+
+    if prec == "f16h":
+        x, y = op.from_h16(x), op.from_h16(y)
+    x64 = x.to(torch.complex128)
+    y64 = op.apply(x64, 0.0, prec="f64")
+    e = ((y.to(torch.complex128) - y64).abs().max() / y64.abs().max()).item()
+    del x64, y64
+    return e
+
+
 def native(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -410,6 +425,8 @@ def native(args, world, rank, local, pg):
                              "measured_peaks_tflops": peaks, "fp32_nominal_tflops": FP32_NOMINAL_TFLOPS},
                      "kernel_hash": kernel_hash()},
         "e2e": e2e,
+        "accuracy": {"max_rel_err": rel_err_vs_fp64(op, x, out, prec) if prec != "f64" else 0.0,
+                     "vs": "FP64 apply of the same input on the same fields (max |out - out64| / max |out64|)"},
         "gpu_launches": int(launches),
         "clocks": ck,
         "wall_s_timed": t_wall,
@@ -440,6 +457,8 @@ def native(args, world, rank, local, pg):
                 sweep["%s/n%d" % (m, nr)] = {"ms": t, "ms_per_rhs": t / nr, "GB/s": b / (t * 1e-3) / 1e9,
                                              "frac_hbm": b / (t * 1e-3) / 1e9 / peak,
                                              "TFLOP/s": method_flops(m) * nr * V / (t * 1e-3) / 1e12}
+                if nr == 1 and p != "f64":
+                    sweep["%s/n%d" % (m, nr)]["max_rel_err"] = rel_err_vs_fp64(op, xx, oo, p)
                 del xx, oo
         line["sweep"] = sweep
     if not args.no_solve and world == 1:
