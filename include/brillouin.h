@@ -416,8 +416,7 @@ bri_status bri_tune(bri_ctx *ctx, bri_prec prec, int nrhs, void *stream);
  * warp takes per pass (an even number 2..12; 0 or anything else: 12).
  * bri_get_threads returns the current choice or a negative bri_status;
  * untuned: the unrolled kernel at 128 threads (BRI_F64); on an x extent of
- * 32, 22528 + 64 (FP32 and FP16 full and 2-row fields) or 22528 + 32
- * (8-parameter fields); otherwise 128 threads with variant 10240 (FP32 full fields), 18432
+ * 32, 22528 + 64 (FP32 and FP16 fields); otherwise 128 threads with variant 10240 (FP32 full fields), 18432
  * (FP32 2-row, FP16 full and 2-row fields) or 12288 (8-parameter fields).  bri_set_threads returns BRI_EINVAL for nrhs < 1, a
  * negative value, 1..31 or more than 1024 threads (other than with 16384), or
  * a variant above 22528. */

@@ -29,10 +29,10 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
 // Untuned launch shape per storage format: FP64 -> unrolled kernel (128
 // threads).  FP32 and FP16 fields on an x extent of 32: the line kernel with
 // the links and neighbour spinors staged by bulk copies (variant 11, one warp
-// per x line), 7-22% faster than the L2-prefetch loops on 32^3x64; for full and
-// 2-row fields in its form with one buffer per spinor line (low bits 64), whose
-// smaller stages leave room for 12 warps per SM instead of 10.  Other extents,
-// 128 threads: the pair loop with
+// per x line) in its form with one buffer per spinor line (low bits 64), whose
+// smaller stages leave room for more warps per SM: 10-24% faster than the
+// L2-prefetch loops on 32^3x64 (FP16 8-parameter fields 1% slower than with
+// the two-deep ring).  Other extents, 128 threads: the pair loop with
 // L2 link prefetch, (d, -d) combined before the gamma terms (variant 5) for
 // FP32 full fields, the same loop with the per-site part of the link addresses
 // computed once and the next pair's neighbours carried over (variant 9) for
@@ -42,7 +42,7 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
 static int default_shape(bri_ctx *ctx, bri_prec prec) {
     if (prec == BRI_F64) return 128;
     const bri_comp c = (prec == BRI_F32 ? ctx->f32 : ctx->f16).comp;
-    if (ctx->g.L[0] == 32) return (c == BRI_LINK_8PARAM ? 32 : 64) | (11 << 11);
+    if (ctx->g.L[0] == 32) return 64 | (11 << 11);
     if (prec == BRI_F32 && c == BRI_LINK_FULL) return 128 | (5 << 11);
     if (c == BRI_LINK_8PARAM) return 128 | (6 << 11);
     return 128 | (9 << 11);

@@ -1006,9 +1006,8 @@ struct LineShift {
 };
 
 template <class LL, bool SB>
-__global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const float2 *__restrict__ in,
-                                                          float2 *__restrict__ out, Geom g, double diag,
-                                                          const int *__restrict__ skip) {
+BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ in, float2 *__restrict__ out,
+                             const Geom &g, double diag, const int *__restrict__ skip) {
     extern __shared__ __align__(128) unsigned char bulk_sm[];
     constexpr uint32_t RUN = LL::RUN_A + LL::RUN_B;
     constexpr uint32_t LSTAGE = 2 * RUN;
@@ -1193,6 +1192,22 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const
     }
     dslash_finish<float2, false>(mode, in, out, site, g, diag, acc);
 }
+// FP32 full fields: the stages allow at most 14 blocks per SM, and the loop
+// without a register cap (144 registers, 3 warps per scheduler) was faster
+template <class LL, bool SB>
+__global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const float2 *__restrict__ in,
+                                                          float2 *__restrict__ out, Geom g, double diag,
+                                                          const int *__restrict__ skip) {
+    dslash_bulk_line2<LL, SB>(mode, ll, in, out, g, diag, skip);
+}
+// the other formats: held to 128 registers (no spills), 4 warps per scheduler
+// (16 per SM) where their smaller stages fit; 2-8% faster than uncapped
+template <class LL, bool SB>
+__global__ void __maxnreg__(128) k_dslash_bulk_line2_r128(int mode, LL ll, const float2 *__restrict__ in,
+                                                          float2 *__restrict__ out, Geom g, double diag,
+                                                          const int *__restrict__ skip) {
+    dslash_bulk_line2<LL, SB>(mode, ll, in, out, g, diag, skip);
+}
 
 // ---- shared-memory tiled variant (FP32 spinors) ------------------------------
 // A CTA owns a TX x TY x TZ x TT tile of sites (one thread per site).  The
@@ -1372,22 +1387,55 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
     dim3 grid;
     if constexpr (sizeof(T) == 8) {
         if (variant == 11 && g.L[0] == 32 && g.s0 % 32 == 0 && g.s1 % 32 == 0) {
-            // line kernel with staged links and spinors, one warp per block
+            // line kernel with staged links and spinors, one warp per block; low
+            // bits 64: one buffer per spinor line
+            grid = dim3((unsigned)((g.s1 - g.s0) / 32) * (unsigned)nrhs);
+            constexpr bool big = LL::RUN_A + LL::RUN_B > 2048;  // FP32 full fields
             static bool l2_attr = false;
             if (!l2_attr) {
-                cudaFuncSetAttribute(k_dslash_bulk_line2<LL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)line2_smem<LL, false>());
-                cudaFuncSetAttribute(k_dslash_bulk_line2<LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)line2_smem<LL, true>());
+                // dynamic shared memory above 48 KB is not needed, but the carveout is:
+                // all of the unified L1 / shared memory as shared memory holds the
+                // stages of 12-16 blocks per SM, and the loop reads nothing through L1
+                if constexpr (big) {
+                    cudaFuncSetAttribute(k_dslash_bulk_line2<LL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)line2_smem<LL, false>());
+                    cudaFuncSetAttribute(k_dslash_bulk_line2<LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)line2_smem<LL, true>());
+                    cudaFuncSetAttribute(k_dslash_bulk_line2<LL, false>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+                    cudaFuncSetAttribute(k_dslash_bulk_line2<LL, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+                } else {
+                    cudaFuncSetAttribute(k_dslash_bulk_line2_r128<LL, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line2_smem<LL, false>());
+                    cudaFuncSetAttribute(k_dslash_bulk_line2_r128<LL, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line2_smem<LL, true>());
+                    cudaFuncSetAttribute(k_dslash_bulk_line2_r128<LL, false>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+                    cudaFuncSetAttribute(k_dslash_bulk_line2_r128<LL, true>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+                }
                 l2_attr = true;
             }
-            grid = dim3((unsigned)((g.s1 - g.s0) / 32) * (unsigned)nrhs);
-            if (threads == 64)
-                k_dslash_bulk_line2<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(mode, ll, (const T *)in,
-                                                                                       (T *)out, g, diag, skip);
-            else
-                k_dslash_bulk_line2<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(mode, ll, (const T *)in,
-                                                                                         (T *)out, g, diag, skip);
+            const bool sb = threads == 64;
+            if constexpr (big) {
+                if (sb)
+                    k_dslash_bulk_line2<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(mode, ll, (const T *)in,
+                                                                                          (T *)out, g, diag, skip);
+                else
+                    k_dslash_bulk_line2<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(mode, ll, (const T *)in,
+                                                                                            (T *)out, g, diag, skip);
+            } else {
+                if (sb)
+                    k_dslash_bulk_line2_r128<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(
+                        mode, ll, (const T *)in, (T *)out, g, diag, skip);
+                else
+                    k_dslash_bulk_line2_r128<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(
+                        mode, ll, (const T *)in, (T *)out, g, diag, skip);
+            }
             return;
         }
         if (variant >= 10 && g.s0 % 32 == 0) {
