@@ -325,11 +325,12 @@ def test_argument_errors(gpu):
         Brillouin((2, 4, 4, 4))
 
 
-@pytest.mark.parametrize("L", [(4, 3, 4, 3), (4, 4, 3, 6), (3, 4, 4, 12)])
+@pytest.mark.parametrize("L", [(4, 3, 4, 3), (4, 4, 3, 6), (3, 4, 4, 12), (32, 3, 3, 8)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_apply_host_buffers_match_device_apply(gpu, L, prec):
     """bri_apply_host (slabs in t, copies overlapping the stencil) gives the
-    device apply bit for bit, pinned or pageable, D and D^dagger, 2 RHS."""
+    device apply bit for bit, pinned or pageable, D and D^dagger, 2 RHS (x
+    extent 32: the bulk-copy line kernel on whole-line site ranges)."""
     U = synth.random_su3_links(L, 0.4, 51)
     op = Brillouin(L, AP)
     op.build_hops(torch.as_tensor(U, device=gpu), prec="f32" if prec == "f32" else "f64", comp="full")
