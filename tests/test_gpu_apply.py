@@ -223,6 +223,36 @@ def test_bulk_copy_kernel_matches_oracle(gpu, prec, comp, L, bc):
             _check(outh[r], ref[r][2], tol, (shape, "H"))
 
 
+@pytest.mark.parametrize("name", ["wilson", "hypercube"])
+@pytest.mark.parametrize("prec,comp", [("f32", "full"), ("f16", "2row")])
+def test_bulk_copy_kernel_other_weights(gpu, name, prec, comp):
+    """The line kernel (launch variant 11, x extent 32) with the Wilson and the
+    hypercube columns of the weight table: the hop list then holds other
+    groups of equal (d_y, d_z, d_t) (Wilson: four single-hop groups), which the
+    kernel's spinor-line staging follows."""
+    L, bc = (32, 3, 3, 4), AP
+    tol = TOL_MAX[(prec, comp)]
+    U, psi, W = _setup(L, bc, 90)
+    lam, rho = WEIGHTS[name]
+    op = Brillouin(L, bc)
+    op.set_weights(lam, rho)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec=prec, comp=comp)
+    x = torch.as_tensor(psi.astype(np.complex64), device=gpu)
+    oracle.set_weights(lam, rho)
+    try:
+        ref = [(oracle.apply(L, bc, W, 0.05, psi[r]), oracle.apply(L, bc, W, 0.05, psi[r], dagger=True))
+               for r in range(psi.shape[0])]
+    finally:
+        oracle.reset_weights()
+    for shape in (11 * 2048 + 32, 11 * 2048 + 64):
+        op.set_threads(prec, 2, shape)
+        out = op.apply(x, m0=0.05, prec=prec).cpu().numpy()
+        outd = op.apply(x, m0=0.05, dagger=True, prec=prec).cpu().numpy()
+        for r in range(psi.shape[0]):
+            _check(out[r], ref[r][0], tol, (shape, name, "D"))
+            _check(outd[r], ref[r][1], tol, (shape, name, "Ddag"))
+
+
 def test_multi_rhs_equals_single(gpu):
     L, bc = (4, 3, 5, 4), AP
     U = synth.random_su3_links(L, 0.3, 5)
