@@ -56,6 +56,61 @@ BRI_D void h16_store(uint4 *__restrict__ d, float *__restrict__ s, int site, con
     s[site] = sc;
 }
 
+// The FP16-spinor storage for the bulk-copy line kernel (x extent 32): a staged
+// x line is the 32 sites' halves (1,536 bytes) followed by their 32 scales
+// (128 bytes), each copied as one run.  Halves at a 48-byte pitch, 3 x 16
+// bytes per site, fall on distinct bank groups for any 8 consecutive slots.
+struct LineSpinH16 {
+    static constexpr uint32_t LINE = 32u * 48u + 128u;
+    static constexpr bool SCALED = true;
+    const uint4 *__restrict__ d;
+    const float *__restrict__ s;
+    uint4 *__restrict__ od;
+    float *__restrict__ os;
+    BRI_D LineSpinH16(const void *i, void *o, int rhs, int V) {
+        const size_t fb = h16_field_bytes(V);
+        const unsigned char *ib = (const unsigned char *)i + rhs * fb;
+        unsigned char *ob = (unsigned char *)o + rhs * fb;
+        d = (const uint4 *)ib;
+        s = (const float *)(ib + (size_t)48 * V);
+        od = (uint4 *)ob;
+        os = (float *)(ob + (size_t)48 * V);
+    }
+    BRI_D void issue1(int ln, uint32_t dst, uint32_t bar) const {
+        bulk_elect2(bar, LINE, dst, d + (size_t)ln * 96, 1536u, dst + 1536u, s + (size_t)ln * 32, 128u);
+    }
+    BRI_D void issue2(int l0, int l1, uint32_t dst, uint32_t bar) const {
+        bulk_elect4(bar, 2 * LINE, dst, d + (size_t)l0 * 96, 1536u, dst + 1536u, s + (size_t)l0 * 32, 128u,
+                    dst + LINE, d + (size_t)l1 * 96, 1536u, dst + LINE + 1536u, s + (size_t)l1 * 32, 128u);
+    }
+    // the halves at a slot (unscaled) and the site's scale: the loop folds the
+    // scale (a power of two) into the pair's coefficients
+    BRI_D float load(uint32_t ln, uint32_t slot, float2 o[12]) const {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const uint4 v = lds4u(ln + 48u * slot + 16u * i);
+            o[4 * i] = h2f(v.x);
+            o[4 * i + 1] = h2f(v.y);
+            o[4 * i + 2] = h2f(v.z);
+            o[4 * i + 3] = h2f(v.w);
+        }
+        return __uint_as_float(lds1u(ln + 1536u + 4u * slot));
+    }
+    BRI_D void finish(int mode, int site, const Geom &g, double diag, const AccF &acc) const {
+        float2 p[12];
+        SpinH16{d, s}.load(site, p);
+        const float dg = (float)diag;
+        float2 o[12];
+#pragma unroll
+        for (int i = 0; i < 12; i++) {
+            o[i].x = dg * p[i].x + acc.a[i].x - acc.ai[i].y;
+            o[i].y = dg * p[i].y + acc.a[i].y + acc.ai[i].x;
+            if (mode == 2 && i >= 6) { o[i].x = -o[i].x; o[i].y = -o[i].y; }
+        }
+        h16_store(od, os, site, o);
+    }
+};
+
 // BODY 2: the gamma terms inside the spin loop (pair_body_s); 3: after it (pair_body)
 template <class LL, int BODY>
 __global__ void k_dslash_h16(int mode, LL ll, const unsigned char *__restrict__ in, unsigned char *__restrict__ out,
@@ -122,6 +177,29 @@ __global__ void k_dslash_h16(int mode, LL ll, const unsigned char *__restrict__ 
 template <class LL, int BODY>
 static void launch_h16(int mode, const LL &ll, const void *in, void *out, int nrhs, const Geom &g, double diag,
                        const int *skip, cudaStream_t s) {
+    if (g.L[0] == 32 && g.s0 % 32 == 0 && g.s1 % 32 == 0) {
+        // the bulk-copy line kernel: links and FP16 spinor lines staged, one
+        // buffer per spinor line, 128 registers
+        constexpr unsigned smem = line2_smem<LL, true, LineSpinH16>();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_dslash_bulk_line2_r128<LL, true, LineSpinH16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_dslash_bulk_line2_r128<LL, true, LineSpinH16>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+            attr = true;
+        }
+        const int nl = (g.s1 - g.s0) / 32;
+        const int rmax = (int)(0x7fffffffULL / (unsigned long long)nl < 65535ULL ? 0x7fffffffULL / nl : 65535ULL);
+        const size_t fb = h16_field_bytes(g.V);
+        for (int r0 = 0; r0 < nrhs; r0 += rmax) {
+            const int nr = nrhs - r0 < rmax ? nrhs - r0 : rmax;
+            k_dslash_bulk_line2_r128<LL, true, LineSpinH16><<<dim3((unsigned)nl * (unsigned)nr), 32, smem, s>>>(
+                mode, ll, (const unsigned char *)in + r0 * fb, (unsigned char *)out + r0 * fb, g, diag,
+                skip ? skip + r0 : nullptr);
+        }
+        return;
+    }
     const int threads = 128;
     const size_t fb = h16_field_bytes(g.V);
     // grid.x holds site blocks x RHS: split the RHS so that it stays below 2^31
@@ -188,6 +266,10 @@ size_t bri_h16_bytes(int V) { return h16_field_bytes(V); }
 // has checked that they exist
 bri_status bri_dslash_h16(bri_ctx *ctx, void *out, const void *in, int nrhs, double m0, int mode, const int *skip,
                           cudaStream_t s) {
+    if (ctx->werr_h && *(volatile int *)ctx->werr_h) {
+        *(volatile int *)ctx->werr_h = 0;
+        return bri_fail(ctx, BRI_ETIMEOUT, "a bounded wait of an earlier apply gave up; its output is invalid");
+    }
     const Geom &g = ctx->g;
     const LinkStore &st = ctx->f16;
     const int VP = (g.V + 31) & ~31;

@@ -996,8 +996,41 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line(int mode, LL ll, const 
 // has consumed its forward spinors, the backward line once it has consumed
 // the backward ones.  That gives up about half a pair of lead for 6 KB less
 // shared memory per warp (13 instead of 10 warps per SM for FP32 full fields).
-template <class LL, bool SB> BRI_HD constexpr unsigned line2_smem() {
-    return 128u + 4u * (LL::RUN_A + LL::RUN_B) + (SB ? 2u : 4u) * 3072u;
+// Spinor storage of the line kernel, FP32: 12 complex per site, one x line
+// (3,072 bytes) copied as one run.  (The FP16-spinor storage is LineSpinH16,
+// next to its apply.)  A policy holds the right-hand side's input and output
+// and provides the line copies, the per-slot load from a staged line and the
+// epilogue.
+struct LineSpinF32 {
+    static constexpr uint32_t LINE = 32u * 96u;
+    static constexpr bool SCALED = false;  // load returns 1
+    const float2 *__restrict__ in;
+    float2 *__restrict__ out;
+    BRI_D LineSpinF32(const void *i, void *o, int rhs, int V)
+        : in((const float2 *)i + (size_t)rhs * V * 12), out((float2 *)o + (size_t)rhs * V * 12) {}
+    BRI_D void issue1(int ln, uint32_t dst, uint32_t bar) const {
+        bulk_elect1(bar, LINE, dst, in + (size_t)ln * 384, LINE);
+    }
+    BRI_D void issue2(int l0, int l1, uint32_t dst, uint32_t bar) const {
+        bulk_elect2(bar, 2 * LINE, dst, in + (size_t)l0 * 384, LINE, dst + LINE, in + (size_t)l1 * 384, LINE);
+    }
+    // the spinor at a slot of a staged line, as q x (returned scale)
+    BRI_D float load(uint32_t ln, uint32_t slot, float2 q[12]) const {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const float4 v = lds4(ln + 96u * slot + 16u * k);
+            q[2 * k] = make_float2(v.x, v.y);
+            q[2 * k + 1] = make_float2(v.z, v.w);
+        }
+        return 1.f;
+    }
+    BRI_D void finish(int mode, int site, const Geom &g, double diag, const AccF &acc) const {
+        dslash_finish<float2, false>(mode, in, out, site, g, diag, acc);
+    }
+};
+
+template <class LL, bool SB, class SP = LineSpinF32> BRI_HD constexpr unsigned line2_smem() {
+    return 128u + 4u * (LL::RUN_A + LL::RUN_B) + (SB ? 2u : 4u) * SP::LINE;
 }
 
 struct LineShift {
@@ -1005,13 +1038,13 @@ struct LineShift {
     float uf, ub;  // boundary phases of their y, z, t wraps
 };
 
-template <class LL, bool SB>
-BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ in, float2 *__restrict__ out,
+template <class LL, bool SB, class SP>
+BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in, void *__restrict__ out,
                              const Geom &g, double diag, const int *__restrict__ skip) {
     extern __shared__ __align__(128) unsigned char bulk_sm[];
     constexpr uint32_t RUN = LL::RUN_A + LL::RUN_B;
     constexpr uint32_t LSTAGE = 2 * RUN;
-    constexpr uint32_t SLINE = 32u * 12u * 8u;  // one x line of FP32 spinors
+    constexpr uint32_t SLINE = SP::LINE;  // one staged x line of spinors
     constexpr uint32_t SSTAGE = 2 * SLINE;
     const int nl = (g.s1 - g.s0) >> 5;
     const int nr = (int)gridDim.x / nl;
@@ -1020,9 +1053,7 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ 
     if (skip && skip[rhs]) return;
     const int lane = (int)threadIdx.x;
     const int site = line * 32 + lane;
-    const size_t off = (size_t)rhs * g.V * 12;
-    in += off;
-    out += off;
+    const SP io(in, out, rhs, g.V);
     // barriers: link stages 0, 1, spinor stages 0, 1 (SB: forward line, backward line)
     const uint32_t lbars = (uint32_t)__cvta_generic_to_shared(bulk_sm);
     const uint32_t sbars = lbars + 16u;
@@ -1064,14 +1095,10 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ 
         ll.bulk_pair(g.hop[t].j, line, bl, lring + LSTAGE * sn, lbars + 8u * sn, extra);
     };
     auto issue_spinors = [&](const LineShift &ls, int sn) {
-        const uint32_t dst = sring + SSTAGE * sn;
-        bulk_elect2(sbars + 8u * sn, 2 * SLINE, dst, in + (size_t)ls.fl * 384, SLINE, dst + SLINE,
-                    in + (size_t)ls.bl * 384, SLINE);
+        io.issue2(ls.fl, ls.bl, sring + SSTAGE * sn, sbars + 8u * sn);
     };
     // SB: one line into buffer k (0 forward, 1 backward)
-    auto issue_line = [&](int ln, int k) {
-        bulk_elect1(sbars + 8u * k, SLINE, sring + SLINE * k, in + (size_t)ln * 384, SLINE);
-    };
+    auto issue_line = [&](int ln, int k) { io.issue1(ln, sring + SLINE * k, sbars + 8u * k); };
     if (nh > 0) {
         LineShift cur = shifts(0), nxt = cur;
         int gend = g.hop[0].ge;  // first pair of the next group
@@ -1133,13 +1160,12 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ 
             {
                 const M3<float2> W = ll.load_run(lk, lane);
                 float2 q[12];
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const float4 v = lds4(sp + 96u * sf + 16u * k);
-                    q[2 * k] = make_float2(v.x, v.y);
-                    q[2 * k + 1] = make_float2(v.z, v.w);
-                }
+                const float scf = io.load(sp, sf, q);
                 colour_mv<1>(W, q, cf);
+                if constexpr (SP::SCALED) {
+#pragma unroll
+                    for (int i = 0; i < 12; i++) cf[i] = __fmul2_rn(cf[i], f2(scf));
+                }
             }
             if (last) {
                 __syncwarp();  // every lane has consumed its forward spinor
@@ -1150,13 +1176,10 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ 
             }
             const M3<float2> W = ll.load_run(lk + RUN, (int)sb);
             float2 q[12];
-#pragma unroll
-            for (int k = 0; k < 6; k++) {
-                const float4 v = lds4(sp + SLINE + 96u * sb + 16u * k);
-                q[2 * k] = make_float2(v.x, v.y);
-                q[2 * k + 1] = make_float2(v.z, v.w);
-            }
-            pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+            // a scaled storage's backward scale goes into the phase factor
+            const float scb = io.load(sp + SLINE, sb, q);
+            pair_body_s(cf, W, q, hc.lam * phf, SP::SCALED ? phf * phb * scb : phf * phb, hc.rho * rsign * phf, hc,
+                        acc);
             if (last) {
                 __syncwarp();  // every lane has consumed its backward spinor
                 issue_line(nxt.bl, 1);
@@ -1190,23 +1213,23 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const float2 *__restrict__ 
             return;
         }
     }
-    dslash_finish<float2, false>(mode, in, out, site, g, diag, acc);
+    io.finish(mode, site, g, diag, acc);
 }
 // FP32 full fields: the stages allow at most 14 blocks per SM, and the loop
 // without a register cap (144 registers, 3 warps per scheduler) was faster
-template <class LL, bool SB>
-__global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const float2 *__restrict__ in,
-                                                          float2 *__restrict__ out, Geom g, double diag,
+template <class LL, bool SB, class SP = LineSpinF32>
+__global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const void *__restrict__ in,
+                                                          void *__restrict__ out, Geom g, double diag,
                                                           const int *__restrict__ skip) {
-    dslash_bulk_line2<LL, SB>(mode, ll, in, out, g, diag, skip);
+    dslash_bulk_line2<LL, SB, SP>(mode, ll, in, out, g, diag, skip);
 }
 // the other formats: held to 128 registers (no spills), 4 warps per scheduler
 // (16 per SM) where their smaller stages fit; 2-8% faster than uncapped
-template <class LL, bool SB>
-__global__ void __maxnreg__(128) k_dslash_bulk_line2_r128(int mode, LL ll, const float2 *__restrict__ in,
-                                                          float2 *__restrict__ out, Geom g, double diag,
+template <class LL, bool SB, class SP = LineSpinF32>
+__global__ void __maxnreg__(128) k_dslash_bulk_line2_r128(int mode, LL ll, const void *__restrict__ in,
+                                                          void *__restrict__ out, Geom g, double diag,
                                                           const int *__restrict__ skip) {
-    dslash_bulk_line2<LL, SB>(mode, ll, in, out, g, diag, skip);
+    dslash_bulk_line2<LL, SB, SP>(mode, ll, in, out, g, diag, skip);
 }
 
 // ---- shared-memory tiled variant (FP32 spinors) ------------------------------
@@ -1423,18 +1446,18 @@ void dslash_launch(int mode, const LL &ll, const void *in, void *out, int nrhs, 
             const bool sb = threads == 64;
             if constexpr (big) {
                 if (sb)
-                    k_dslash_bulk_line2<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(mode, ll, (const T *)in,
-                                                                                          (T *)out, g, diag, skip);
+                    k_dslash_bulk_line2<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(mode, ll, in, out, g, diag,
+                                                                                          skip);
                 else
-                    k_dslash_bulk_line2<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(mode, ll, (const T *)in,
-                                                                                            (T *)out, g, diag, skip);
+                    k_dslash_bulk_line2<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(mode, ll, in, out, g,
+                                                                                            diag, skip);
             } else {
                 if (sb)
-                    k_dslash_bulk_line2_r128<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(
-                        mode, ll, (const T *)in, (T *)out, g, diag, skip);
+                    k_dslash_bulk_line2_r128<LL, true><<<grid, 32, line2_smem<LL, true>(), s>>>(mode, ll, in, out, g,
+                                                                                               diag, skip);
                 else
-                    k_dslash_bulk_line2_r128<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(
-                        mode, ll, (const T *)in, (T *)out, g, diag, skip);
+                    k_dslash_bulk_line2_r128<LL, false><<<grid, 32, line2_smem<LL, false>(), s>>>(mode, ll, in, out,
+                                                                                                 g, diag, skip);
             }
             return;
         }

@@ -54,8 +54,10 @@ def test_h16_conversion_follows_its_definition(gpu, L, nrhs):
 
 
 @pytest.mark.parametrize("comp", ["full", "2row", "8param"])
-@pytest.mark.parametrize("L,nrhs", [((3, 3, 3, 3), 3), ((3, 5, 4, 6), 2), ((4, 4, 4, 6), 1)])
+@pytest.mark.parametrize("L,nrhs", [((3, 3, 3, 3), 3), ((3, 5, 4, 6), 2), ((4, 4, 4, 6), 1), ((32, 3, 4, 4), 2)])
 def test_h16_apply_matches_oracle(gpu, comp, L, nrhs):
+    """x extent 32: the bulk-copy line kernel with the FP16 spinor lines
+    staged (halves and scales); otherwise the pair loop."""
     U = synth.random_su3_links(L, 0.4, 40 + sum(L))
     psi = synth.gaussian_spinor(L, nrhs, 41 + sum(L)).astype(np.complex64)
     W = oracle.build_hops(L, U)
