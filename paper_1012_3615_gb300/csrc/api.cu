@@ -43,6 +43,13 @@ static bri_status check_prec(bri_ctx *ctx, bri_prec p) {
 }
 
 // ---- tuning cache file: one "key threads" line per entry ----------------------
+// a launch shape bri_set_threads accepts: threads per block in the low 11 bits
+// (0 or 32..1024; for the tensor-core variant 8 the RHS per warp pass), kernel
+// variant above them (0..11)
+static bool valid_shape(int threads) {
+    const int thr = threads & 2047, variant = threads >> 11;
+    return threads >= 0 && variant <= 11 && (variant == 8 || !((thr > 0 && thr < 32) || thr > 1024));
+}
 static void tune_load(bri_ctx *ctx) {
     const char *f = getenv("BRI_TUNE_CACHE");
     if (!f || !*f) return;
@@ -50,7 +57,7 @@ static void tune_load(bri_ctx *ctx) {
     std::string key;
     int thr;
     while (in >> key >> thr)
-        if (thr > 0 && thr <= 1024) ctx->tune[key] = thr;
+        if (valid_shape(thr)) ctx->tune[key] = thr;
 }
 static void tune_save_entry(const std::string &key, int thr) {
     const char *f = getenv("BRI_TUNE_CACHE");
@@ -445,8 +452,7 @@ bri_status bri_set_threads(bri_ctx *ctx, bri_prec prec, int nrhs, int threads) {
     if (!ctx) return BRI_EINVAL;
     BRI_RETURN_IF(check_prec(ctx, prec));
     const int thr = threads & 2047, variant = threads >> 11;
-    if (nrhs < 1 || threads < 0 || variant > 11 || (variant != 8 && ((thr > 0 && thr < 32) || thr > 1024)))
-        return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
+    if (nrhs < 1 || !valid_shape(threads)) return bri_fail(ctx, BRI_EINVAL, "bad nrhs or threads");
     // variant 8 (tensor cores): the low bits are the right-hand sides per warp pass
     ctx->tune[bri_tune_key(ctx, prec, nrhs)] = variant == 8 ? threads : (thr & ~31) | (variant << 11);
     return BRI_OK;

@@ -388,3 +388,31 @@ def test_many_right_hand_sides(gpu):
     many = op.apply(x, 0.2, prec="f32")
     for r in (0, 1, 499, 998, 999):
         assert torch.equal(many[r:r + 1], op.apply(x[r:r + 1].contiguous(), 0.2, prec="f32"))
+
+
+def test_tuner_choice_is_correct_and_cached(gpu, tmp_path, monkeypatch):
+    """bri_tune times its candidate launch shapes (the bulk-copy variants
+    among them on an x extent of 32) and keeps the fastest; the apply with that
+    shape matches the oracle, the choice is appended to BRI_TUNE_CACHE, and a
+    new context reads it back, variant bits included."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("BRI_TUNE_CACHE", str(cache))
+    L, bc = (32, 3, 4, 4), AP
+    U, psi, W = _setup(L, bc, 95)
+    op = Brillouin(L, bc)
+    op.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp="2row")
+    op.tune("f32", 2)
+    shape = op.threads("f32", 2)
+    assert shape >= 0
+    out = op.apply(torch.as_tensor(psi.astype(np.complex64), device=gpu), 0.05, prec="f32").cpu().numpy()
+    for r in range(psi.shape[0]):
+        _check(out[r], oracle.apply(L, bc, W, 0.05, psi[r]), TOL_MAX[("f32", "2row")], ("tuned", shape))
+    assert cache.read_text().split()[-1] == str(shape)
+    op2 = Brillouin(L, bc)
+    op2.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp="2row")
+    assert op2.threads("f32", 2) == shape
+    # a cached shape with the variant bits of the line kernel survives the reload
+    cache.write_text(cache.read_text() + "dslash:32x3x4x4:p1:c1:n3 %d\n" % (11 * 2048 + 64))
+    op3 = Brillouin(L, bc)
+    op3.build_hops(torch.as_tensor(U, device=gpu), prec="f32", comp="2row")
+    assert op3.threads("f32", 3) == 11 * 2048 + 64
