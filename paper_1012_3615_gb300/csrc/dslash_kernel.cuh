@@ -988,14 +988,16 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line(int mode, LL ll, const 
 // psi(x - d) at slot (x - d_x) mod 32 of the backward one, and its boundary
 // phase is the group's (uniform) y, z, t part times its own x part; the lines
 // and phases are worked out once per group.  The loop has no global loads and
-// no per-lane neighbour arithmetic left.  Needs an x extent of 32 and s0, s1
-// multiples of 32.  Dynamic shared memory: line2_smem<LL, SB>().
+// no per-lane neighbour arithmetic left.  All copies are issued by one lane
+// that elect.sync picks from the converged warp.  Needs an x extent of 32 and
+// s0, s1 multiples of 32.  Dynamic shared memory: line2_smem<LL, SB, SP>().
 //
 // SB = true keeps one buffer per spinor line instead of a two-deep ring: the
 // forward line of the next group is copied as soon as the group's last pair
 // has consumed its forward spinors, the backward line once it has consumed
 // the backward ones.  That gives up about half a pair of lead for 6 KB less
-// shared memory per warp (13 instead of 10 warps per SM for FP32 full fields).
+// shared memory per warp (12 instead of 10 warps per SM for FP32 full fields).
+
 // Spinor storage of the line kernel, FP32: 12 complex per site, one x line
 // (3,072 bytes) copied as one run.  (The FP16-spinor storage is LineSpinH16,
 // next to its apply.)  A policy holds the right-hand side's input and output
