@@ -378,10 +378,11 @@ def test_apply_host_buffers_match_device_apply(gpu, L, prec):
             assert torch.equal(got, want)
 
 
-def test_many_right_hand_sides(gpu):
-    """1000 right-hand sides in one launch on a 3^4 lattice (grid of site
-    blocks x RHS): every RHS equals its own single apply."""
-    L = (3, 3, 3, 3)
+@pytest.mark.parametrize("L", [(3, 3, 3, 3), (32, 3, 3, 3)])
+def test_many_right_hand_sides(gpu, L):
+    """1000 right-hand sides in one launch (grid of site blocks, or x lines for
+    the line kernel on an x extent of 32, times RHS): every RHS equals its own
+    single apply."""
     op = Brillouin(L, AP)
     op.build_hops(torch.as_tensor(synth.random_su3_links(L, 0.5, 71), device=gpu), prec="f32")
     x = synth.gaussian_spinor_torch(L, 1000, 72, device=gpu).to(torch.complex64)
