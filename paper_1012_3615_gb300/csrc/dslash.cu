@@ -30,9 +30,9 @@ std::string bri_tune_key(bri_ctx *ctx, bri_prec prec, int nrhs) {
 // threads).  FP32 and FP16 fields on an x extent of 32: the line kernel with
 // the links and neighbour spinors staged by bulk copies (variant 11, one warp
 // per x line) in its form with one buffer per spinor line (low bits 64), whose
-// smaller stages leave room for more warps per SM: 10-24% faster than the
-// L2-prefetch loops on 32^3x64 (FP16 8-parameter fields 1% slower than with
-// the two-deep ring).  Other extents, 128 threads: the pair loop with
+// smaller stages leave room for more warps per SM: 10-20% faster than the
+// L2-prefetch loops on 32^3x64 and 0.2-10% faster than with the two-deep
+// ring.  Other extents, 128 threads: the pair loop with
 // L2 link prefetch, (d, -d) combined before the gamma terms (variant 5) for
 // FP32 full fields, the same loop with the per-site part of the link addresses
 // computed once and the next pair's neighbours carried over (variant 9) for

@@ -158,7 +158,7 @@ __global__ void k_dslash_h16(int mode, LL ll, const unsigned char *__restrict__ 
         float2 q[12];
         sp.load(yb, q);
         if constexpr (BODY == 3) pair_body(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
-        else pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+        else pair_body_s<false>(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
     }
     float2 p[12];
     sp.load(site, p);

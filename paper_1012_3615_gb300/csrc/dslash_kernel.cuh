@@ -260,8 +260,14 @@ BRI_D void pair_body(float2 cf[12], const M3<float2> &W, const float2 p[12], flo
 // terms are taken once per pair on the difference instead of once per hop, which
 // saves 12 (n - 1) packed FMAs per pair of class n.  cf holds chi_f; W and p are
 // the reversed hop's field and spinor; L = lam phf, R = rsign rho phf.
+// ALLMU = false takes the gamma terms of the directions with d_mu != 0 under
+// warp-uniform branches; ALLMU = true takes all four with zero coefficients
+// where d_mu = 0 (12 (4 - n) more packed FMAs, no branch inside the pair),
+// which leaves the compiler one block to schedule and fewer live registers
+// (the line kernel with FP32 full fields: 126 instead of 144).
+template <bool ALLMU>
 BRI_D void pair_body_s(const float2 cf[12], const M3<float2> &W, const float2 p[12], float L, float q, float R,
-                     const HopArg &h, AccF &acc) {
+                       const HopArg &h, AccF &acc) {
     float2 A[9], B[9];
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -292,7 +298,7 @@ BRI_D void pair_body_s(const float2 cf[12], const M3<float2> &W, const float2 p[
         for (int c = 0; c < 3; c++) acc.a[3 * sp + c] = __ffma2_rn(f2(L), sm[c], acc.a[3 * sp + c]);
 #pragma unroll
         for (int mu = 0; mu < 4; mu++) {
-            if (h.dm[mu] == 0) continue;  // uniform across the warp
+            if (!ALLMU && h.dm[mu] == 0) continue;  // uniform across the warp
             const int s = gcol(mu, sp);
             const int gr = gre(mu, s), gi = gim(mu, s);
             const float cfm = gr != 0 ? (gr > 0 ? rd[mu] : -rd[mu]) : (gi > 0 ? rd[mu] : -rd[mu]);
@@ -338,7 +344,9 @@ BRI_D void f32_hops(const LL &ll, const float2 *__restrict__ in, int site, const
             float2 q[12];
             load_spinor(in + (size_t)yb * 12, q);
             if constexpr (BODY == 3) pair_body(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
-            else pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+            else
+                pair_body_s<LL::COMP != BRI_LINK_8PARAM>(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc,
+                                                         acc);
         }
     } else if constexpr (!PF && BODY == 1) {
 #pragma unroll 1
@@ -453,7 +461,7 @@ BRI_D void f32_hops_lean(const LL &ll, const float2 *__restrict__ in, int site, 
         const M3<float2> W = ll.load_ci(hc.j, cbc, cyb);
         float2 q[12];
         load_spinor(in + (size_t)cyb * 12, q);
-        pair_body_s(cf, W, q, hc.lam * cphf, cphf * cphb, hc.rho * rsign * cphf, hc, acc);
+        pair_body_s<LL::COMP == BRI_LINK_2ROW>(cf, W, q, hc.lam * cphf, cphf * cphb, hc.rho * rsign * cphf, hc, acc);
     }
 }
 
@@ -592,7 +600,7 @@ BRI_D bool f32_hops_bulk(const LL &ll, const float2 *__restrict__ in, int site, 
         else W = ll.load(hc.j, yb);
         float2 q[12];
         load_spinor(in + (size_t)yb * 12, q);
-        pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+        pair_body_s<false>(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
         if (++s == ST) { s = 0; par ^= 1u; }
     }
     return true;
@@ -805,7 +813,10 @@ BRI_D void dslash_body(int mode, const LL &ll, const typename LL::T *__restrict_
         } else if constexpr (VAR == 9) {
             f32_hops_lean(ll, in, site, nb, rsign, g, acc);
         } else {
-            // VAR 5 (and 6, through k_dslash_r128): pair_body_s; VAR 7: pair_body
+            // VAR 5 (and 6, through k_dslash_r128): pair_body_s; VAR 7: pair_body.
+            // The branch-free gamma terms (pair_body_s<true>) measured 1-2% faster
+            // in variants 5 and 9 for full and 2-row fields, and 1-3% slower for
+            // 8-parameter fields and, in variant 9, FP16 full ones
             f32_hops<VAR == 1 || VAR >= 5, VAR == 4 ? 1 : VAR == 5 ? 2 : VAR == 7 ? 3 : 0>(ll, in, site, nb, rsign, g,
                                                                                           acc);
         }
@@ -968,7 +979,7 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line(int mode, LL ll, const 
         const M3<float2> W = ll.load_run(cur + RUN, yb & 31);
         float2 q[12];
         load_spinor(in + (size_t)yb * 12, q);
-        pair_body_s(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
+        pair_body_s<false>(cf, W, q, hc.lam * phf, phf * phb, hc.rho * rsign * phf, hc, acc);
         if (++s == ST) { s = 0; par ^= 1u; }
     }
     if (!ok) {
@@ -992,11 +1003,10 @@ __global__ void __launch_bounds__(32) k_dslash_bulk_line(int mode, LL ll, const 
 // that elect.sync picks from the converged warp.  Needs an x extent of 32 and
 // s0, s1 multiples of 32.  Dynamic shared memory: line2_smem<LL, SB, SP>().
 //
-// SB = true keeps one buffer per spinor line instead of a two-deep ring: the
-// forward line of the next group is copied as soon as the group's last pair
-// has consumed its forward spinors, the backward line once it has consumed
-// the backward ones.  That gives up about half a pair of lead for 6 KB less
-// shared memory per warp (12 instead of 10 warps per SM for FP32 full fields).
+// SB = true keeps one buffer per spinor line instead of a two-deep ring: both
+// lines of the next group are copied once the group's last pair has consumed
+// its spinors.  That gives up about a pair of lead for 6 KB less shared memory
+// per warp (14 instead of 10 warps per SM for FP32 full fields).
 
 // Spinor storage of the line kernel, FP32: 12 complex per site, one x line
 // (3,072 bytes) copied as one run.  (The FP16-spinor storage is LineSpinH16,
@@ -1140,10 +1150,14 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
             }
             if (!mbar_wait(lbars + 8u * s, (uint32_t)(t >> 1) & 1u, BULK_WAIT_NS)) return false;
             // (waiting on the spinor stage at every pair, not just the group's
-            // first, measured faster: the conditional form takes 13 more registers)
+            // first, measured faster: the conditional form takes 13 more registers;
+            // SB: both lines are waited for here, before any load of the pair, so
+            // that the pair's loads and arithmetic form one block without a wait
+            // or branch in between: 0.3% faster alone, 5% with pair_body_s<true>)
             uint32_t sp;  // the group's forward line; its backward line follows at + SLINE
             if constexpr (SB) {
                 if (!mbar_wait(sbars, (uint32_t)gi & 1u, BULK_WAIT_NS)) return false;
+                if (!mbar_wait(sbars + 8u, (uint32_t)gi & 1u, BULK_WAIT_NS)) return false;
                 sp = sring;
             } else {
                 if (!mbar_wait(sbars + 8u * (uint32_t)(gi & 1), (uint32_t)(gi >> 1) & 1u, BULK_WAIT_NS))
@@ -1156,7 +1170,7 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
             const float phb = cur.ub * (dx > 0 ? e0 : dx < 0 ? e31 : 1.f);
             const uint32_t lk = lring + LSTAGE * (uint32_t)s;
             const uint32_t sf = (uint32_t)((lane + dx) & 31), sb = (uint32_t)((lane - dx) & 31);
-            // SB: the group's last pair releases each line buffer to the next group
+            // SB: the group's last pair releases both line buffers to the next group
             const bool last = SB && t + 1 == gend && gend < nh;
             float2 cf[12];
             {
@@ -1169,21 +1183,15 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
                     for (int i = 0; i < 12; i++) cf[i] = __fmul2_rn(cf[i], f2(scf));
                 }
             }
-            if (last) {
-                __syncwarp();  // every lane has consumed its forward spinor
-                issue_line(nxt.fl, 0);
-            }
-            if constexpr (SB) {
-                if (!mbar_wait(sbars + 8u, (uint32_t)gi & 1u, BULK_WAIT_NS)) return false;
-            }
             const M3<float2> W = ll.load_run(lk + RUN, (int)sb);
             float2 q[12];
             // a scaled storage's backward scale goes into the phase factor
             const float scb = io.load(sp + SLINE, sb, q);
-            pair_body_s(cf, W, q, hc.lam * phf, SP::SCALED ? phf * phb * scb : phf * phb, hc.rho * rsign * phf, hc,
-                        acc);
+            pair_body_s<true>(cf, W, q, hc.lam * phf, SP::SCALED ? phf * phb * scb : phf * phb, hc.rho * rsign * phf,
+                              hc, acc);
             if (last) {
-                __syncwarp();  // every lane has consumed its backward spinor
+                __syncwarp();  // every lane has consumed its spinors
+                issue_line(nxt.fl, 0);
                 issue_line(nxt.bl, 1);
             }
             return true;
@@ -1217,8 +1225,8 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
     }
     io.finish(mode, site, g, diag, acc);
 }
-// FP32 full fields: the stages allow at most 14 blocks per SM, and the loop
-// without a register cap (144 registers, 3 warps per scheduler) was faster
+// FP32 full fields: the stages allow at most 14 blocks per SM (126 registers
+// without a cap; the two-deep spinor ring: 150, 3 warps per scheduler)
 template <class LL, bool SB, class SP = LineSpinF32>
 __global__ void __launch_bounds__(32) k_dslash_bulk_line2(int mode, LL ll, const void *__restrict__ in,
                                                           void *__restrict__ out, Geom g, double diag,

@@ -208,6 +208,7 @@ struct LinkF64 {
 
 template <bri_comp C> struct LinkF32 {
     using T = float2;
+    static constexpr bri_comp COMP = C;
     // 16-byte shared-memory slots one field occupies when prefetched
     static constexpr int SLOTS = C == BRI_LINK_FULL ? 5 : C == BRI_LINK_2ROW ? 3 : 2;
     static constexpr int NQ = C == BRI_LINK_FULL ? 4 : C == BRI_LINK_2ROW ? 3 : 2;  // float4 chunks
@@ -346,6 +347,7 @@ template <bri_comp C> struct LinkF32 {
 
 template <bri_comp C> struct LinkF16 {
     using T = float2;
+    static constexpr bri_comp COMP = C;
     static constexpr int SLOTS = C == BRI_LINK_FULL ? 3 : C == BRI_LINK_2ROW ? 2 : 1;
     static constexpr int NQ = C == BRI_LINK_FULL ? 2 : 1;  // uint4 chunks
     const uint4 *__restrict__ a;
