@@ -333,6 +333,11 @@ def native(args, world, rank, local, pg):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"metric": "mixed/batched vs FP64 solve time to 1e-10", "unit": "s",
+                              "solve": solve_bench(args, dev)}), flush=True)
+        return
     mode, nrhs = args.mode, args.nrhs
     prec, comp = mode.split("-")
     L = tuple(args.lattice) if args.lattice else L_BENCH
@@ -743,6 +748,8 @@ def main():
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="leave out the solver workloads (time to 1e-10)")
     ap.add_argument("--solve-small", action="store_true", help="only the 16^3x32 solver workload")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="run only the solver workloads and print their results (no apply timing)")
     ap.add_argument("--fp64-sources", type=int, default=12,
                     help="point sources of the 24^3x48 workload solved in FP64 for the comparison (1-12)")
     ap.add_argument("--rows", action="store_true", help="add hop precompute, FP64 apply and force timings")
