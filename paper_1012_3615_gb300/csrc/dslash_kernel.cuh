@@ -1102,7 +1102,6 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
         return r;
     };
     // the copies are issued by one elected lane of the converged warp
-    // (the copies are issued by one elected lane of the converged warp)
     auto issue_links = [&](int t, int bl, int sn, uint32_t extra) {
         ll.bulk_pair(g.hop[t].j, line, bl, lring + LSTAGE * sn, lbars + 8u * sn, extra);
     };
@@ -1139,13 +1138,20 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
                 if (gend < nh) {
                     nxt = shifts(gend);
                     if constexpr (!SB) {
-                        __syncwarp();  // the stage of group gi + 1 is the one group gi - 1 used
+                        // the stage of group gi + 1 is the one group gi - 1 used: the
+                        // proxy fence orders the lanes' reads of it (generic proxy)
+                        // before the bulk copy into it (async proxy)
+                        fence_async_smem();
+                        __syncwarp();
                         issue_spinors(nxt, (gi + 1) & 1);
                     }
                 }
             }
             if (t + 1 < nh) {
-                __syncwarp();  // every lane has read the link stage pair t - 1 used
+                // every lane has read the link stage pair t - 1 used; those reads
+                // precede the group-boundary branch above, so they are complete
+                // here without a proxy fence (one measured 1.2% slower)
+                __syncwarp();
                 issue_links(t + 1, t + 1 < gend ? cur.bl : nxt.bl, s ^ 1, 0u);
             }
             if (!mbar_wait(lbars + 8u * s, (uint32_t)(t >> 1) & 1u, BULK_WAIT_NS)) return false;
@@ -1190,7 +1196,12 @@ BRI_D void dslash_bulk_line2(int mode, const LL &ll, const void *__restrict__ in
             pair_body_s<true>(cf, W, q, hc.lam * phf, SP::SCALED ? phf * phb * scb : phf * phb, hc.rho * rsign * phf,
                               hc, acc);
             if (last) {
-                __syncwarp();  // every lane has consumed its spinors
+                // every lane has read its spinors: the proxy fence orders those
+                // reads (generic proxy) before the copies into the same buffers
+                // (async proxy); without it a copy issued right after the reads
+                // can overwrite a line before it is read
+                fence_async_smem();
+                __syncwarp();
                 issue_line(nxt.fl, 0);
                 issue_line(nxt.bl, 1);
             }
