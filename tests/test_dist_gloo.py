@@ -5,6 +5,7 @@ import socket
 
 import pytest
 import torch.multiprocessing as mp
+from mp_util import collect
 
 
 def _free_port():
@@ -36,10 +37,7 @@ def test_max_over_ranks_with_gloo():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    for p in procs:
-        p.join(timeout=120)
-        assert p.exitcode == 0
-    out = dict(q.get(timeout=10) for _ in range(2))
+    out = dict(collect(q, procs, 2, 300))
     assert out == {0: 2.5, 1: 2.5}
 
 

@@ -10,6 +10,7 @@ import socket
 import numpy as np
 import pytest
 import torch.multiprocessing as mp
+from mp_util import collect
 
 
 def _free_port():
@@ -55,10 +56,7 @@ def test_two_rank_halo_apply_equals_single_domain(L, grid, bc):
     procs = [ctx.Process(target=_worker, args=(r, 2, port, L, grid, bc, q)) for r in range(2)]
     for p in procs:
         p.start()
-    got = [q.get(timeout=300) for _ in range(2)]
-    for p in procs:
-        p.join(timeout=120)
-        assert p.exitcode == 0
+    got = collect(q, procs, 2, 300)
     U = synth.random_su3_links(L, 0.4, 7)
     psi = synth.gaussian_spinor(L, 1, 8)[0]
     ref = oracle.apply(L, bc, oracle.build_hops(L, U), 0.07, psi)

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 import torch.multiprocessing as mp
+from mp_util import collect
 
 from paper_1012_3615_gb300 import Brillouin, synth
 
@@ -65,10 +66,7 @@ def test_two_ranks_on_the_gpu_equal_the_single_domain_apply(gpu, L, grid, bc):
     procs = [ctx.Process(target=_worker, args=(r, 2, port, L, grid, bc, q)) for r in range(2)]
     for p in procs:
         p.start()
-    got = [q.get(timeout=600) for _ in range(2)]
-    for p in procs:
-        p.join(timeout=120)
-        assert p.exitcode == 0
+    got = collect(q, procs, 2, 600)
     op = Brillouin(L, bc)
     op.build_hops(torch.as_tensor(synth.random_su3_links(L, 0.4, 31), device=gpu), prec="f32")
     x = torch.as_tensor(synth.gaussian_spinor(L, 1, 32), device=gpu)
